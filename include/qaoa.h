@@ -1,0 +1,238 @@
+/*
+ * qaoa.h -- C ABI of the GB300 (sm_103a) QAOA state-vector simulator.
+ *
+ * The method is "Fast Simulation of High-Depth QAOA Circuits" (arXiv
+ * 2309.04841): precompute the diagonal cost vector f(x) over all 2^n basis
+ * states (Sec. 3.1), then apply p layers of the phase operator
+ * exp(-i gamma_l f) (elementwise, Algorithm 3) and the transverse-field mixer
+ * exp(-i beta_l sum_q X_q) (Algorithms 1-2), and reduce the objective
+ * <psi|diag(f)|psi> and the ground-state overlap (Sec. 3.1, Sec. 4).
+ *
+ * Conventions (all entry points):
+ *   - qubit q (0 <= q < n) is bit q of the basis index x; spin
+ *     s_q(x) = +1 if bit q is 0, -1 if it is 1.
+ *   - the mixer gate is exp(-i beta X) = [[cos b, -i sin b], [-i sin b, cos b]].
+ *   - states are interleaved complex: float2 (QAOA_C64) or double2
+ *     (QAOA_C128) per amplitude, 2^n amplitudes, index x.
+ *   - cost vectors hold 2^n values of type int32, float32 or float64.
+ *   - every device pointer is owned by the caller (allocate it with any CUDA
+ *     allocator, e.g. a torch tensor); the library never allocates device
+ *     memory and never frees a pointer it is given.  Cost and state buffers
+ *     must be 16-byte aligned, workspaces 256-byte aligned.
+ *   - calls enqueue work on `stream` and return without synchronising, unless
+ *     the comment says "synchronises".  Results written to device pointers
+ *     are valid once the stream reaches that point.
+ *   - on any error the call returns a status, enqueues nothing further and
+ *     leaves the outputs untouched; it never aborts or traps.  Errors of
+ *     kernels that already ran asynchronously surface as QAOA_ERR_CUDA at the
+ *     next synchronising call.
+ *   - 1 <= n <= QAOA_MAX_N.  Calls are thread-safe if they use distinct
+ *     workspaces; calls that share a workspace must be ordered on one stream.
+ */
+#ifndef QAOA_H
+#define QAOA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QAOA_MAX_N 34
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *qaoa_stream_t;
+
+typedef enum {
+    QAOA_OK = 0,
+    QAOA_ERR_INVALID_ARG = 1,   /* bad size, pointer, enum, angle or term  */
+    QAOA_ERR_OUT_OF_MEMORY = 2, /* caller-provided buffer too small        */
+    QAOA_ERR_OVERFLOW = 3,      /* integer cost would not fit int32        */
+    QAOA_ERR_CUDA = 4,          /* a CUDA runtime call or kernel failed    */
+    QAOA_ERR_TIMEOUT = 5,       /* a bounded wait ran out                  */
+    QAOA_ERR_REJECTED = 6,      /* serving: request can never be admitted  */
+    QAOA_ERR_CANCELLED = 7,     /* serving: request was cancelled          */
+    QAOA_ERR_NOT_FOUND = 8,     /* serving: unknown ticket                 */
+    QAOA_ERR_BUSY = 9           /* serving: queue full, retry later        */
+} qaoa_status;
+
+typedef enum { QAOA_COST_I32 = 0, QAOA_COST_F32 = 1, QAOA_COST_F64 = 2 } qaoa_cost_type;
+typedef enum { QAOA_C64 = 0, QAOA_C128 = 1 } qaoa_state_type;
+
+/*
+ * One term of the cost polynomial f(s) = sum_k w_k prod_{i in t_k} s_i
+ * (Eq. 1).  Bit i of `mask` set <=> variable i is in t_k.  mask == 0 is the
+ * constant offset term.
+ */
+typedef struct {
+    double weight;
+    uint64_t mask;
+} qaoa_term;
+
+/* Statistics of a cost vector that later calls need. */
+typedef struct {
+    double f_min;    /* min_x f[x]                                   */
+    double f_max;    /* max_x f[x]                                   */
+    uint64_t n_min;  /* number of x with f[x] == f_min (ground states) */
+} qaoa_cost_stats;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *qaoa_status_string(qaoa_status st);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int qaoa_version(void);
+
+/* Message describing the last error returned on the calling thread (static
+ * thread-local buffer, "" if none). */
+const char *qaoa_last_error_message(void);
+
+/* ------------------------------------------------------------ host helpers */
+
+/*
+ * LABS terms (Background, "Low Autocorrelation Binary Sequences"):
+ * f = sum_{k=1}^{n-1} C_k^2 with C_k = sum_i s_i s_{i+k}, written as
+ * 4-body terms of weight 4, 2-body terms of weight 2 and a constant n(n-1)/2
+ * (twice the paper's reduced polynomial plus n(n-1)/2).  Writes at most `cap`
+ * terms to `out` (host) and the total count to *n_out; if cap is too small
+ * returns QAOA_ERR_OUT_OF_MEMORY with *n_out set.  `out` may be NULL when
+ * cap == 0.  n <= 64.
+ */
+qaoa_status qaoa_labs_terms(int n, qaoa_term *out, size_t cap, size_t *n_out);
+
+/*
+ * Weighted MaxCut terms (Background): f = sum_{(i,j)} (w_ij / 2)(s_i s_j - 1)
+ * = -(cut weight), as m two-body terms of weight w/2 and one constant
+ * -sum(w)/2.  edges: host array of 2m int32 (i, j), 0 <= i, j < n, i != j;
+ * w: host array of m doubles (NULL means all 1).  Output as qaoa_labs_terms.
+ */
+qaoa_status qaoa_maxcut_terms(int n, const int32_t *edges, const double *w,
+                              size_t m, qaoa_term *out, size_t cap,
+                              size_t *n_out);
+
+/* --------------------------------------------------------- a1: cost vector */
+
+/*
+ * Cost vector from terms (Sec. 3.1, Eq. 1; Algorithm 3 step 1):
+ * d_costs[x] = sum_k w_k (-1)^popcount(x & mask_k), for all x < 2^n.
+ *   terms: host array of n_terms terms; every mask < 2^n.
+ *   QAOA_COST_I32: every weight must be an integer and sum |w_k| < 2^31
+ *     (QAOA_ERR_OVERFLOW otherwise); the result is exact.
+ *   QAOA_COST_F32 / F64: the sum is formed as in float64 in term order and
+ *     rounded once to the output type; when every weight is a multiple of
+ *     2^-e with sum |w_k| 2^e < 2^53 the sum is exact (order-independent).
+ *     QAOA_COST_F32 takes at most 1024 terms.
+ *   d_costs: device, 2^n elements of the cost type.
+ */
+qaoa_status qaoa_precompute_costs(int n, const qaoa_term *terms, size_t n_terms,
+                                  qaoa_cost_type ct, void *d_costs,
+                                  qaoa_stream_t stream);
+
+/*
+ * LABS cost vector directly from the autocorrelations (Background):
+ * d_costs[x] = sum_{k=1}^{n-1} (n - k - 2 popcount((x ^ (x >> k)) & (2^{n-k}-1)))^2,
+ * int32, exact; O(n) per x instead of O(n^2) terms.  n <= 32.
+ */
+qaoa_status qaoa_labs_costs(int n, int32_t *d_costs, qaoa_stream_t stream);
+
+/*
+ * Weighted MaxCut cost vector directly from the edge list (Background):
+ * d_costs[x] = -sum_{(i,j) cut by x} w_ij, accumulated in edge order as in
+ * float64 (exact when the weights are dyadic as for qaoa_precompute_costs).
+ * edges/w as qaoa_maxcut_terms (host).  QAOA_COST_I32 needs integer weights
+ * with sum |w| < 2^31.  m <= 1536.
+ */
+qaoa_status qaoa_maxcut_costs(int n, const int32_t *edges, const double *w,
+                              size_t m, qaoa_cost_type ct, void *d_costs,
+                              qaoa_stream_t stream);
+
+/*
+ * Minimum, maximum and number of minimisers of a cost vector.  d_work is a
+ * device workspace of at least qaoa_workspace_bytes(n) bytes.  Writes the
+ * result to *h_out (host).  Synchronises `stream`.
+ */
+qaoa_status qaoa_cost_stats_compute(int n, const void *d_costs,
+                                    qaoa_cost_type ct, void *d_work,
+                                    size_t work_bytes, qaoa_cost_stats *h_out,
+                                    qaoa_stream_t stream);
+
+/* ------------------------------------------------------------- workspace */
+
+/*
+ * Bytes of device workspace (reduction partials and counters) that the calls
+ * below need for n qubits; the same workspace serves every call on one stream.
+ */
+size_t qaoa_workspace_bytes(int n);
+
+/* ---------------------------------------------------- a2-a4: simulation */
+
+/*
+ * Algorithm 3: p layers of  psi <- exp(-i beta_l sum X) exp(-i gamma_l f) psi.
+ *   d_costs/ct: the cost vector; stats: from qaoa_cost_stats_compute on it
+ *     (host struct; only f_min/f_max are read).
+ *   gammas, betas: host arrays of p finite doubles, 1 <= p <= 100000.
+ *   d_state: device, 2^n amplitudes of type st, updated in place.  If
+ *     init_plus != 0 the input is ignored and the simulation starts from
+ *     |+>^n (Background), otherwise from the state in d_state.
+ *   d_work/work_bytes: device workspace (qaoa_workspace_bytes(n)).
+ *   d_out: device, 2 doubles, or NULL.  If non-NULL, receives
+ *     [E, O] = [sum_x |psi_x|^2 f_x, sum_{x: f_x = f_min} |psi_x|^2] of the
+ *     final state (Sec. 3.1 inner product; Sec. 4 get_overlap), fused into
+ *     the last pass.
+ * Asynchronous.
+ */
+qaoa_status qaoa_simulate(int n, const void *d_costs, qaoa_cost_type ct,
+                          const qaoa_cost_stats *stats, const double *gammas,
+                          const double *betas, int p, void *d_state,
+                          qaoa_state_type st, int init_plus, void *d_work,
+                          size_t work_bytes, double *d_out,
+                          qaoa_stream_t stream);
+
+/* ---------------------------------------------------- a5: reductions */
+
+/*
+ * Expectation sum_x |psi_x|^2 f_x (Sec. 3.1) of the state in d_state, written
+ * to d_out[0] (device double).  Deterministic order.  Asynchronous.
+ */
+qaoa_status qaoa_expectation(int n, const void *d_state, qaoa_state_type st,
+                             const void *d_costs, qaoa_cost_type ct,
+                             void *d_work, size_t work_bytes, double *d_out,
+                             qaoa_stream_t stream);
+
+/*
+ * Ground-state overlap sum_{x: f_x = stats->f_min} |psi_x|^2 (Sec. 4,
+ * get_overlap with the cost vector as the default), written to d_out[0].
+ * Asynchronous.
+ */
+qaoa_status qaoa_overlap(int n, const void *d_state, qaoa_state_type st,
+                         const void *d_costs, qaoa_cost_type ct,
+                         const qaoa_cost_stats *stats, void *d_work,
+                         size_t work_bytes, double *d_out,
+                         qaoa_stream_t stream);
+
+/* ---------------------------------------------------- a6: adjoint gradient */
+
+/*
+ * Objective and gradient with respect to all 2p angles (not in the paper):
+ * forward simulation from |+>^n, then one backward sweep that un-applies the
+ * layers in place on two state vectors (psi and lambda = d E / d psi^*),
+ * accumulating
+ *   dE/dbeta_l  = 2 Im <lambda| sum_q X_q |psi>   inside the un-mixer passes,
+ *   dE/dgamma_l = 2 Im <lambda| f |psi>          before each un-phase.
+ *   d_state, d_lambda: device, 2^n amplitudes each (contents ignored and
+ *     overwritten; on return d_state holds approximately |+>^n).
+ *   d_out: device, 2 + 2p doubles: [E, O, dE/dgamma_1..p, dE/dbeta_1..p],
+ *     E and O of the forward final state.
+ * Asynchronous.
+ */
+qaoa_status qaoa_grad(int n, const void *d_costs, qaoa_cost_type ct,
+                      const qaoa_cost_stats *stats, const double *gammas,
+                      const double *betas, int p, void *d_state,
+                      void *d_lambda, qaoa_state_type st, void *d_work,
+                      size_t work_bytes, double *d_out, qaoa_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QAOA_H */

@@ -13,7 +13,6 @@ SRC = os.path.join(HERE, "oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
 
-
 def _native(path):
     """True if the ELF file at path was built for this machine's architecture."""
     import platform
@@ -25,6 +24,7 @@ def _native(path):
     except OSError:
         return False
     return len(hdr) == 20 and hdr[:4] == b"\x7fELF" and (want is None or hdr[18] == want)
+
 
 def build(force: bool = False) -> str:
     if (not force and os.path.exists(LIB) and _native(LIB)

@@ -1,0 +1,710 @@
+// api.cu -- C ABI entry points (include/qaoa.h) and the host-side pass planner.
+//
+// The planner turns one call into a short sequence of kernel launches on the
+// caller's stream:
+//   n <= 12          : single-CTA kernels with the whole state on chip;
+//   n >  12 (tiled)  : per layer one LOW pass (phase + the TB lowest qubits)
+//                      and ceil((n - TB) / (TB - 4)) HIGH passes (the other
+//                      qubits, TB - 4 at a time, 2^4-amplitude segments);
+//                      the adjoint repeats the same shapes in reverse.
+// Nothing here allocates device memory: scratch lives in the caller's
+// workspace, per-layer constants travel in the kernel parameter blocks.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "../../include/qaoa.h"
+#include "kernels.h"
+#include "qaoa_common.cuh"
+
+using namespace qaoa;
+
+namespace {
+
+thread_local char g_errmsg[256] = "";
+
+qaoa_status fail(qaoa_status st, const char *msg) {
+  snprintf(g_errmsg, sizeof(g_errmsg), "%s", msg);
+  return st;
+}
+
+qaoa_status cuda_fail(cudaError_t e, const char *where) {
+  snprintf(g_errmsg, sizeof(g_errmsg), "%s: %s", where, cudaGetErrorString(e));
+  return QAOA_ERR_CUDA;
+}
+
+#define CK(expr, where)                       \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return cuda_fail(_e, where); \
+  } while (0)
+
+int num_sms() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 148;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+bool aligned16(const void *p) { return p && ((uintptr_t)p & 15u) == 0; }
+
+bool valid_cost_type(qaoa_cost_type ct) {
+  return ct == QAOA_COST_I32 || ct == QAOA_COST_F32 || ct == QAOA_COST_F64;
+}
+
+bool valid_state_type(qaoa_state_type st) { return st == QAOA_C64 || st == QAOA_C128; }
+
+// Workspace layout: [0, 256) counters, [256, 512) small outputs, then partials.
+constexpr size_t kWsCounters = 0, kWsSmall = 256, kWsPartials = 512;
+
+size_t partial_doubles(int n) {
+  const size_t tiles = n > 11 ? ((size_t)1 << (n - 11)) : 1;  // smallest tile: 2^11
+  size_t need = tiles * 3;
+  const size_t red = (size_t)1024 * 3;  // cost-stats / expectation grids
+  return need > red ? need : red;
+}
+
+struct Ws {
+  unsigned *counter;
+  double *small;
+  double *partials;
+};
+
+qaoa_status get_ws(int n, void *d_work, size_t bytes, Ws &ws) {
+  if (!d_work || ((uintptr_t)d_work & 255u)) return fail(QAOA_ERR_INVALID_ARG, "workspace must be 256-byte aligned and non-NULL");
+  if (bytes < qaoa_workspace_bytes(n)) return fail(QAOA_ERR_OUT_OF_MEMORY, "workspace smaller than qaoa_workspace_bytes(n)");
+  char *b = reinterpret_cast<char *>(d_work);
+  ws.counter = reinterpret_cast<unsigned *>(b + kWsCounters);
+  ws.small = reinterpret_cast<double *>(b + kWsSmall);
+  ws.partials = reinterpret_cast<double *>(b + kWsPartials);
+  return QAOA_OK;
+}
+
+qaoa_status check_angles(const double *g, const double *b, int p) {
+  if (p < 1 || p > 100000) return fail(QAOA_ERR_INVALID_ARG, "p must be in [1, 100000]");
+  if (!g || !b) return fail(QAOA_ERR_INVALID_ARG, "NULL angle array");
+  for (int i = 0; i < p; ++i)
+    if (!std::isfinite(g[i]) || !std::isfinite(b[i])) return fail(QAOA_ERR_INVALID_ARG, "non-finite angle");
+  return QAOA_OK;
+}
+
+const double kTwoPi = 6.283185307179586476925286766559;
+
+// Phase data for multiplying by exp(-i g f).
+template <typename Real>
+void make_phase(PhaseData<Real> &ph, double g, qaoa_cost_type ct, const qaoa_cost_stats *stats) {
+  using C2 = typename C2T<Real>::type;
+  memset(&ph, 0, sizeof(ph));
+  const double range = stats ? stats->f_max - stats->f_min : 1e300;
+  if (ct == QAOA_COST_I32 && stats && range >= 0 && range < 65536.0) {
+    ph.mode = 0;
+    ph.fmin = (int)stats->f_min;
+    ph.nhi = (int)(range / 256.0) + 1;
+    for (int j = 0; j < 256; ++j) {
+      const double a = g * (double)j;
+      ph.tab_lo[j] = C2{(Real)cos(a), (Real)-sin(a)};
+      const double b = g * ((double)stats->f_min + 256.0 * (double)j);
+      ph.tab_hi[j] = C2{(Real)cos(b), (Real)-sin(b)};
+    }
+  } else {
+    ph.mode = 1;
+    const double g2 = g / kTwoPi;
+    ph.g2pi = g2;
+    ph.g_hi = (float)g2;
+    ph.g_lo = (float)(g2 - (double)ph.g_hi);
+  }
+}
+
+// Rotation schedule of one sweep over the tile bits in `set`.
+template <class PL>
+Sweep make_sweep(uint32_t set, bool ascending) {
+  Sweep s;
+  memset(&s, 0, sizeof(s));
+  uint32_t done = 0;
+  for (int k = 0; k < PL::NR; ++k) {
+    const int r = ascending ? k : PL::NR - 1 - k;
+    const uint32_t regs = PL::reg(r);
+    const uint32_t m = regs & set & ~done;
+    done |= m;
+    uint8_t bits = 0;
+    int i = 0;
+    for (int b = 0; b < 32; ++b)
+      if ((regs >> b) & 1u) {
+        if ((m >> b) & 1u) bits |= (uint8_t)(1u << i);
+        ++i;
+      }
+    s.m[r] = bits;
+  }
+  return s;
+}
+
+struct Group {
+  bool high;
+  int c, h;          // geometry
+  uint32_t rot;      // tile bits rotated
+};
+
+// LOW group + HIGH groups covering qubits [TB, n) (TB - 4 per pass).
+std::vector<Group> plan_groups(int n, int TB) {
+  std::vector<Group> gs;
+  gs.push_back(Group{false, TB, TB, (1u << TB) - 1u});
+  const int span = TB - kHighC;
+  for (int q0 = TB; q0 < n;) {
+    const int len = (n - q0) < span ? (n - q0) : span;
+    const int h = q0 < n - span ? q0 : n - span;
+    uint32_t rot = 0;
+    for (int j = kHighC; j < TB; ++j) {
+      const int xb = h + j - kHighC;
+      if (xb >= q0 && xb < q0 + len) rot |= 1u << j;
+    }
+    gs.push_back(Group{true, kHighC, h, rot});
+    q0 += len;
+  }
+  return gs;
+}
+
+Geom make_geom(int n, const Group &G, int TB) {
+  Geom g;
+  g.n = n;
+  g.tb = TB;
+  g.c = G.c;
+  g.h = G.h;
+  g.ntiles = 1ull << (n - TB);
+  return g;
+}
+
+template <typename Real>
+SmallLayer<Real> small_layer(double gamma, double beta) {
+  SmallLayer<Real> L;
+  L.cb = (Real)cos(beta);
+  L.sb = (Real)sin(beta);
+  const double g2 = gamma / kTwoPi;
+  L.g2pi = g2;
+  L.g_hi = (float)g2;
+  L.g_lo = (float)(g2 - (double)L.g_hi);
+  return L;
+}
+
+int cost_kind(qaoa_cost_type ct) { return (int)ct; }
+
+// ----------------------------------------------------------- small path
+
+template <typename Real>
+qaoa_status small_forward(int n, const void *cost, qaoa_cost_type ct, double fmin,
+                          const double *gam, const double *bet, int p, void *state, int init_plus,
+                          double *d_out, cudaStream_t s) {
+  using C2 = typename C2T<Real>::type;
+  for (int l0 = 0; l0 < p; l0 += kSmallMaxLayers) {
+    const int nl = (p - l0) < kSmallMaxLayers ? (p - l0) : kSmallMaxLayers;
+    SmallParams<Real> P;
+    memset(&P, 0, sizeof(P));
+    P.psi = reinterpret_cast<C2 *>(state);
+    P.lam = nullptr;
+    P.cost = cost;
+    P.cost_kind = cost_kind(ct);
+    P.n = n;
+    P.nl = nl;
+    P.mode = 0;
+    P.init_plus = (l0 == 0) && init_plus;
+    P.amp = (Real)(1.0 / sqrt(ldexp(1.0, n)));
+    P.reduce = (l0 + nl == p) && d_out != nullptr;
+    P.fmin_d = fmin;
+    P.out = d_out;
+    for (int i = 0; i < nl; ++i) P.L[i] = small_layer<Real>(gam[l0 + i], bet[l0 + i]);
+    CK(launch_small(P, s), "small forward launch");
+  }
+  return QAOA_OK;
+}
+
+template <typename Real>
+qaoa_status small_grad(int n, const void *cost, qaoa_cost_type ct, double fmin, const double *gam,
+                       const double *bet, int p, void *state, void *lam, double *d_out,
+                       cudaStream_t s) {
+  using C2 = typename C2T<Real>::type;
+  const Real amp = (Real)(1.0 / sqrt(ldexp(1.0, n)));
+  if (p <= kSmallMaxLayers) {
+    SmallParams<Real> P;
+    memset(&P, 0, sizeof(P));
+    P.psi = reinterpret_cast<C2 *>(state);
+    P.lam = reinterpret_cast<C2 *>(lam);
+    P.cost = cost;
+    P.cost_kind = cost_kind(ct);
+    P.n = n;
+    P.nl = p;
+    P.mode = 1;
+    P.init_plus = 1;
+    P.amp = amp;
+    P.reduce = 1;
+    P.fmin_d = fmin;
+    P.out = d_out;
+    P.out_dg = d_out + 2;
+    P.out_db = d_out + 2 + p;
+    for (int i = 0; i < p; ++i) P.L[i] = small_layer<Real>(gam[i], bet[i]);
+    CK(launch_small(P, s), "small grad launch");
+    return QAOA_OK;
+  }
+  qaoa_status st = small_forward<Real>(n, cost, ct, fmin, gam, bet, p, state, 1, d_out, s);
+  if (st != QAOA_OK) return st;
+  const int nchunks = (p + kSmallMaxLayers - 1) / kSmallMaxLayers;
+  for (int ci = nchunks - 1; ci >= 0; --ci) {
+    const int l0 = ci * kSmallMaxLayers;
+    const int nl = (p - l0) < kSmallMaxLayers ? (p - l0) : kSmallMaxLayers;
+    SmallParams<Real> P;
+    memset(&P, 0, sizeof(P));
+    P.psi = reinterpret_cast<C2 *>(state);
+    P.lam = reinterpret_cast<C2 *>(lam);
+    P.cost = cost;
+    P.cost_kind = cost_kind(ct);
+    P.n = n;
+    P.nl = nl;
+    P.mode = 2;
+    P.init_lambda = (ci == nchunks - 1);
+    P.amp = amp;
+    P.fmin_d = fmin;
+    P.out_dg = d_out + 2 + l0;
+    P.out_db = d_out + 2 + p + l0;
+    for (int i = 0; i < nl; ++i) P.L[i] = small_layer<Real>(gam[l0 + i], bet[l0 + i]);
+    CK(launch_small(P, s), "small adjoint launch");
+  }
+  return QAOA_OK;
+}
+
+// ----------------------------------------------------------- tiled path
+
+template <typename Real> struct FwdTB;
+template <> struct FwdTB<float> { using Low = PlanF13Low; using High = PlanF13High; };
+template <> struct FwdTB<double> { using Low = PlanT12Low; using High = PlanT12High; };
+template <typename Real> struct BwdTB;
+template <> struct BwdTB<float> { using Low = PlanT12Low; using High = PlanT12High; };
+template <> struct BwdTB<double> { using Low = PlanT11Low; using High = PlanT11High; };
+
+template <typename Real>
+qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                          const double *gam, const double *bet, int p, void *state, int init_plus,
+                          const Ws &ws, double *d_out, cudaStream_t s) {
+  using C2 = typename C2T<Real>::type;
+  using Low = typename FwdTB<Real>::Low;
+  using High = typename FwdTB<Real>::High;
+  const int TB = Low::TB;
+  const std::vector<Group> gs = plan_groups(n, TB);
+  const int nsm = num_sms();
+  if (d_out) CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
+  FwdParams<Real> P;
+  for (int l = 0; l < p; ++l) {
+    for (size_t gi = 0; gi < gs.size(); ++gi) {
+      const Group &G = gs[gi];
+      memset(&P, 0, sizeof(P));
+      P.psi = reinterpret_cast<C2 *>(state);
+      P.cost = cost;
+      P.cost_kind = cost_kind(ct);
+      P.g = make_geom(n, G, TB);
+      P.s1 = Sweep{{0, 0, 0, 0}};
+      P.s2 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
+      P.c2 = (Real)cos(bet[l]);
+      P.s2s = (Real)sin(bet[l]);
+      P.has_phase = (gi == 0);
+      if (P.has_phase) make_phase<Real>(P.ph, gam[l], ct, stats);
+      P.init_plus = (l == 0 && gi == 0 && init_plus);
+      P.amp = (Real)(1.0 / sqrt(ldexp(1.0, n)));
+      P.reduce = (l == p - 1 && gi + 1 == gs.size() && d_out != nullptr);
+      P.fmin_d = stats ? stats->f_min : 0.0;
+      P.partials = ws.partials;
+      P.counter = ws.counter;
+      P.out = d_out;
+      CK(launch_fwd(P, G.high, s, nsm), "forward pass launch");
+    }
+  }
+  return QAOA_OK;
+}
+
+template <typename Real>
+qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                           const double *gam, const double *bet, int p, void *state, void *lam,
+                           const Ws &ws, double *d_grad_g, double *d_grad_b, cudaStream_t s) {
+  using C2 = typename C2T<Real>::type;
+  using Low = typename BwdTB<Real>::Low;
+  using High = typename BwdTB<Real>::High;
+  const int TB = Low::TB;
+  const std::vector<Group> gs = plan_groups(n, TB);
+  const int nsm = num_sms();
+  CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
+  BwdParams<Real> P;
+  bool first = true;
+  for (int l = p - 1; l >= 0; --l) {
+    for (int gi = (int)gs.size() - 1; gi >= 0; --gi) {
+      const Group &G = gs[gi];
+      memset(&P, 0, sizeof(P));
+      P.psi = reinterpret_cast<C2 *>(state);
+      P.lam = reinterpret_cast<C2 *>(lam);
+      P.cost = cost;
+      P.cost_kind = cost_kind(ct);
+      P.g = make_geom(n, G, TB);
+      P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
+      P.s2 = Sweep{{0, 0, 0, 0}};
+      P.c1 = (Real)cos(bet[l]);
+      P.s1s = (Real)-sin(bet[l]);
+      P.has_phase = (gi == 0);
+      if (P.has_phase) make_phase<Real>(P.ph, -gam[l], ct, stats);
+      P.init_lambda = first;
+      first = false;
+      P.partials = ws.partials;
+      P.counter = ws.counter;
+      P.out_b1 = d_grad_b + l;
+      P.out_g = P.has_phase ? d_grad_g + l : nullptr;
+      P.out_b2 = nullptr;
+      CK(launch_bwd(P, G.high, s, nsm), "adjoint pass launch");
+    }
+  }
+  return QAOA_OK;
+}
+
+qaoa_status check_common(int n, const void *cost, qaoa_cost_type ct, const void *state,
+                         qaoa_state_type st) {
+  if (n < 1 || n > QAOA_MAX_N) return fail(QAOA_ERR_INVALID_ARG, "n out of range");
+  if (!valid_cost_type(ct)) return fail(QAOA_ERR_INVALID_ARG, "bad cost type");
+  if (!valid_state_type(st)) return fail(QAOA_ERR_INVALID_ARG, "bad state type");
+  if (!aligned16(cost)) return fail(QAOA_ERR_INVALID_ARG, "cost pointer NULL or not 16-byte aligned");
+  if (!aligned16(state)) return fail(QAOA_ERR_INVALID_ARG, "state pointer NULL or not 16-byte aligned");
+  return QAOA_OK;
+}
+
+// Decide how to accumulate real weights exactly: if every weight is an
+// integer multiple of 2^-e and sum |w| 2^e < 2^53, integer fixed point.
+bool dyadic_scale(const double *w, size_t m, int *e_out) {
+  int e = 0;
+  for (size_t i = 0; i < m; ++i) {
+    if (w[i] == 0.0) continue;
+    int ex;
+    const double fr = frexp(w[i], &ex);  // w = fr * 2^ex, 0.5 <= |fr| < 1
+    // smallest k with fr * 2^53 divisible: count trailing zero bits of mantissa
+    int64_t mant = (int64_t)ldexp(fr, 53);
+    int tz = 0;
+    while (tz < 53 && (mant & 1) == 0) {
+      mant >>= 1;
+      ++tz;
+    }
+    const int need = 53 - tz - ex;  // w * 2^need is an integer
+    if (need > e) e = need;
+  }
+  if (e > 200) return false;
+  double tot = 0.0;
+  for (size_t i = 0; i < m; ++i) tot += fabs(ldexp(w[i], e));
+  if (!(tot < 9007199254740992.0)) return false;
+  *e_out = e;
+  return true;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+const char *qaoa_status_string(qaoa_status st) {
+  switch (st) {
+    case QAOA_OK: return "ok";
+    case QAOA_ERR_INVALID_ARG: return "invalid argument";
+    case QAOA_ERR_OUT_OF_MEMORY: return "buffer too small";
+    case QAOA_ERR_OVERFLOW: return "integer cost overflow";
+    case QAOA_ERR_CUDA: return "CUDA error";
+    case QAOA_ERR_TIMEOUT: return "timeout";
+    case QAOA_ERR_REJECTED: return "rejected";
+    case QAOA_ERR_CANCELLED: return "cancelled";
+    case QAOA_ERR_NOT_FOUND: return "not found";
+    case QAOA_ERR_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+const char *qaoa_last_error_message(void) { return g_errmsg; }
+
+int qaoa_version(void) { return 100; }
+
+size_t qaoa_workspace_bytes(int n) {
+  if (n < 1) n = 1;
+  if (n > QAOA_MAX_N) n = QAOA_MAX_N;
+  return kWsPartials + partial_doubles(n) * sizeof(double);
+}
+
+qaoa_status qaoa_labs_terms(int n, qaoa_term *out, size_t cap, size_t *n_out) {
+  if (n < 1 || n > 64 || !n_out) return fail(QAOA_ERR_INVALID_ARG, "labs_terms: bad n or n_out");
+  // sum_k C_k^2 = sum_k sum_{i,j} s_i s_{i+k} s_j s_{j+k}: the i == j parts give
+  // the constant sum_k (n - k) = n(n-1)/2; every unordered product of four
+  // distinct spins {i, i+k, j, j+k} (i < j, j != i + k) is a 4-body term and
+  // products with j == i + k collapse to the 2-body term s_i s_{i+2k}.  Terms
+  // with the same index set are merged.
+  std::map<uint64_t, double> acc;  // ordered by mask: deterministic output
+  auto add = [&](uint64_t mask, double w) { acc[mask] += w; };
+  add(0, (double)n * (n - 1) / 2.0);
+  for (int k = 1; k < n; ++k)
+    for (int i = 0; i + k < n; ++i)
+      for (int j = i + 1; j + k < n; ++j) {
+        const uint64_t m = (1ull << i) ^ (1ull << (i + k)) ^ (1ull << j) ^ (1ull << (j + k));
+        add(m, 2.0);  // ordered pairs (i, j) and (j, i)
+      }
+  size_t cnt = 0;
+  for (auto &t : acc)
+    if (t.second != 0.0) ++cnt;
+  *n_out = cnt;
+  if (cap < cnt) return fail(QAOA_ERR_OUT_OF_MEMORY, "labs_terms: cap too small");
+  if (cnt && !out) return fail(QAOA_ERR_INVALID_ARG, "labs_terms: NULL out");
+  size_t k = 0;
+  for (auto &t : acc)
+    if (t.second != 0.0) out[k++] = qaoa_term{t.second, t.first};
+  return QAOA_OK;
+}
+
+qaoa_status qaoa_maxcut_terms(int n, const int32_t *edges, const double *w, size_t m,
+                              qaoa_term *out, size_t cap, size_t *n_out) {
+  if (n < 2 || n > 64 || !n_out || (m && !edges)) return fail(QAOA_ERR_INVALID_ARG, "maxcut_terms: bad arguments");
+  double tot = 0.0;
+  for (size_t e = 0; e < m; ++e) {
+    const int i = edges[2 * e], j = edges[2 * e + 1];
+    if (i < 0 || j < 0 || i >= n || j >= n || i == j) return fail(QAOA_ERR_INVALID_ARG, "maxcut_terms: bad edge");
+    const double we = w ? w[e] : 1.0;
+    if (!std::isfinite(we)) return fail(QAOA_ERR_INVALID_ARG, "maxcut_terms: non-finite weight");
+    tot += we;
+  }
+  *n_out = m + 1;
+  if (cap < m + 1) return fail(QAOA_ERR_OUT_OF_MEMORY, "maxcut_terms: cap too small");
+  if (!out) return fail(QAOA_ERR_INVALID_ARG, "maxcut_terms: NULL out");
+  for (size_t e = 0; e < m; ++e) {
+    const double we = w ? w[e] : 1.0;
+    out[e] = qaoa_term{0.5 * we, (1ull << edges[2 * e]) | (1ull << edges[2 * e + 1])};
+  }
+  out[m] = qaoa_term{-0.5 * tot, 0};
+  return QAOA_OK;
+}
+
+qaoa_status qaoa_precompute_costs(int n, const qaoa_term *terms, size_t n_terms, qaoa_cost_type ct,
+                                  void *d_costs, qaoa_stream_t stream) {
+  if (n < 1 || n > QAOA_MAX_N) return fail(QAOA_ERR_INVALID_ARG, "n out of range");
+  if (!valid_cost_type(ct) || !aligned16(d_costs)) return fail(QAOA_ERR_INVALID_ARG, "bad cost type or pointer");
+  if (n_terms && !terms) return fail(QAOA_ERR_INVALID_ARG, "NULL terms");
+  const uint64_t lim = n == 64 ? ~0ull : ((1ull << n) - 1ull);
+  std::vector<double> w(n_terms);
+  for (size_t k = 0; k < n_terms; ++k) {
+    if ((terms[k].mask & ~lim) != 0) return fail(QAOA_ERR_INVALID_ARG, "term mask has a bit >= n");
+    if (!std::isfinite(terms[k].weight)) return fail(QAOA_ERR_INVALID_ARG, "non-finite weight");
+    w[k] = terms[k].weight;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int nsm = num_sms();
+  int mode;
+  double scale = 1.0;
+  int e_fix = 0;
+  if (ct == QAOA_COST_I32) {
+    double tot = 0.0;
+    for (size_t k = 0; k < n_terms; ++k) {
+      if (w[k] != nearbyint(w[k])) return fail(QAOA_ERR_INVALID_ARG, "I32 costs need integer weights");
+      tot += fabs(w[k]);
+    }
+    if (!(tot < 2147483648.0)) return fail(QAOA_ERR_OVERFLOW, "sum |w| does not fit int32");
+    mode = kTermI32;
+  } else {
+    if (dyadic_scale(w.data(), n_terms, &e_fix)) {
+      mode = kTermFixed;
+      scale = ldexp(1.0, e_fix);
+    } else {
+      mode = kTermF64;
+    }
+    if (ct == QAOA_COST_F32 && n_terms > (size_t)kTermChunk)
+      return fail(QAOA_ERR_INVALID_ARG, "float32 costs take at most 1024 terms per call");
+  }
+  static TermChunk P;  // large parameter block; calls are serialised below
+  static std::mutex *mu = new std::mutex();
+  std::lock_guard<std::mutex> lock(*mu);
+  const size_t nchunks = n_terms ? (n_terms + kTermChunk - 1) / kTermChunk : 1;
+  for (size_t c = 0; c < nchunks; ++c) {
+    memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.mode = mode;
+    P.out_kind = (int)ct;
+    P.accumulate = c > 0;
+    P.scale = scale;
+    P.inv_scale = 1.0 / scale;
+    P.out = d_costs;
+    const size_t k0 = c * kTermChunk;
+    const size_t k1 = (k0 + kTermChunk < n_terms) ? k0 + kTermChunk : n_terms;
+    P.nterms = (int)(k1 - k0);
+    for (size_t k = k0; k < k1; ++k) {
+      P.mask[k - k0] = terms[k].mask;
+      P.wd[k - k0] = w[k];
+      P.wl[k - k0] = (int64_t)(mode == kTermFixed ? ldexp(w[k], e_fix) : w[k]);
+    }
+    CK(launch_terms(P, s, nsm), "cost terms launch");
+  }
+  return QAOA_OK;
+}
+
+qaoa_status qaoa_labs_costs(int n, int32_t *d_costs, qaoa_stream_t stream) {
+  if (n < 2 || n > 32) return fail(QAOA_ERR_INVALID_ARG, "labs_costs: n must be in [2, 32]");
+  if (!aligned16(d_costs)) return fail(QAOA_ERR_INVALID_ARG, "labs_costs: bad pointer");
+  CK(launch_labs(n, d_costs, reinterpret_cast<cudaStream_t>(stream), num_sms()), "labs launch");
+  return QAOA_OK;
+}
+
+qaoa_status qaoa_maxcut_costs(int n, const int32_t *edges, const double *w, size_t m,
+                              qaoa_cost_type ct, void *d_costs, qaoa_stream_t stream) {
+  if (n < 2 || n > QAOA_MAX_N || !valid_cost_type(ct) || !aligned16(d_costs))
+    return fail(QAOA_ERR_INVALID_ARG, "maxcut_costs: bad n, type or pointer");
+  if (m > (size_t)kEdgeMax || (m && !edges)) return fail(QAOA_ERR_INVALID_ARG, "maxcut_costs: too many edges or NULL");
+  std::vector<double> wv(m);
+  for (size_t e = 0; e < m; ++e) {
+    const int i = edges[2 * e], j = edges[2 * e + 1];
+    if (i < 0 || j < 0 || i >= n || j >= n || i == j) return fail(QAOA_ERR_INVALID_ARG, "maxcut_costs: bad edge");
+    wv[e] = w ? w[e] : 1.0;
+    if (!std::isfinite(wv[e])) return fail(QAOA_ERR_INVALID_ARG, "maxcut_costs: non-finite weight");
+  }
+  static EdgeChunk P;
+  static std::mutex *mu = new std::mutex();
+  std::lock_guard<std::mutex> lock(*mu);
+  memset(&P, 0, sizeof(P));
+  P.n = n;
+  P.m = (int)m;
+  P.out_kind = (int)ct;
+  P.out = d_costs;
+  int e2 = 0;
+  if (ct == QAOA_COST_I32) {
+    double tot = 0.0;
+    for (size_t e = 0; e < m; ++e) {
+      if (wv[e] != nearbyint(wv[e])) return fail(QAOA_ERR_INVALID_ARG, "I32 costs need integer weights");
+      tot += fabs(wv[e]);
+    }
+    if (!(tot < 2147483648.0)) return fail(QAOA_ERR_OVERFLOW, "sum |w| does not fit int32");
+    P.mode = kTermI32;
+  } else if (dyadic_scale(wv.data(), m, &e2)) {
+    P.mode = kTermFixed;
+    P.inv_scale = ldexp(1.0, -e2);
+  } else {
+    P.mode = kTermF64;
+  }
+  for (size_t e = 0; e < m; ++e) {
+    P.ei[e] = (uint8_t)edges[2 * e];
+    P.ej[e] = (uint8_t)edges[2 * e + 1];
+    P.wd[e] = wv[e];
+    P.wl[e] = (int64_t)(P.mode == kTermFixed ? ldexp(wv[e], e2) : wv[e]);
+  }
+  CK(launch_maxcut(P, reinterpret_cast<cudaStream_t>(stream), num_sms()), "maxcut launch");
+  return QAOA_OK;
+}
+
+qaoa_status qaoa_cost_stats_compute(int n, const void *d_costs, qaoa_cost_type ct, void *d_work,
+                                    size_t work_bytes, qaoa_cost_stats *h_out, qaoa_stream_t stream) {
+  if (n < 1 || n > QAOA_MAX_N || !valid_cost_type(ct) || !aligned16(d_costs) || !h_out)
+    return fail(QAOA_ERR_INVALID_ARG, "cost_stats: bad arguments");
+  Ws ws;
+  qaoa_status st = get_ws(n, d_work, work_bytes, ws);
+  if (st != QAOA_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
+  CK(launch_cost_stats(n, d_costs, cost_kind(ct), ws.partials, ws.counter, ws.small, s, num_sms()),
+     "cost stats launch");
+  double h[3];
+  CK(cudaMemcpyAsync(h, ws.small, sizeof(h), cudaMemcpyDeviceToHost, s), "cost stats copy");
+  CK(cudaStreamSynchronize(s), "cost stats sync");
+  h_out->f_min = h[0];
+  h_out->f_max = h[1];
+  h_out->n_min = (uint64_t)h[2];
+  return QAOA_OK;
+}
+
+qaoa_status qaoa_simulate(int n, const void *d_costs, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                          const double *gammas, const double *betas, int p, void *d_state,
+                          qaoa_state_type st, int init_plus, void *d_work, size_t work_bytes,
+                          double *d_out, qaoa_stream_t stream) {
+  qaoa_status r = check_common(n, d_costs, ct, d_state, st);
+  if (r != QAOA_OK) return r;
+  if (!stats) return fail(QAOA_ERR_INVALID_ARG, "NULL stats");
+  r = check_angles(gammas, betas, p);
+  if (r != QAOA_OK) return r;
+  if (d_out && ((uintptr_t)d_out & 7u)) return fail(QAOA_ERR_INVALID_ARG, "d_out not 8-byte aligned");
+  Ws ws;
+  r = get_ws(n, d_work, work_bytes, ws);
+  if (r != QAOA_OK) return r;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n <= kSmallMaxN) {
+    return st == QAOA_C64
+               ? small_forward<float>(n, d_costs, ct, stats->f_min, gammas, betas, p, d_state, init_plus, d_out, s)
+               : small_forward<double>(n, d_costs, ct, stats->f_min, gammas, betas, p, d_state, init_plus, d_out, s);
+  }
+  return st == QAOA_C64
+             ? tiled_forward<float>(n, d_costs, ct, stats, gammas, betas, p, d_state, init_plus, ws, d_out, s)
+             : tiled_forward<double>(n, d_costs, ct, stats, gammas, betas, p, d_state, init_plus, ws, d_out, s);
+}
+
+qaoa_status qaoa_expectation(int n, const void *d_state, qaoa_state_type st, const void *d_costs,
+                             qaoa_cost_type ct, void *d_work, size_t work_bytes, double *d_out,
+                             qaoa_stream_t stream) {
+  qaoa_status r = check_common(n, d_costs, ct, d_state, st);
+  if (r != QAOA_OK) return r;
+  if (!d_out) return fail(QAOA_ERR_INVALID_ARG, "NULL d_out");
+  Ws ws;
+  r = get_ws(n, d_work, work_bytes, ws);
+  if (r != QAOA_OK) return r;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
+  CK(launch_expect(n, d_state, st == QAOA_C128, d_costs, cost_kind(ct), 0.0, ws.partials, ws.counter,
+                   d_out, 0, s, num_sms()),
+     "expectation launch");
+  return QAOA_OK;
+}
+
+qaoa_status qaoa_overlap(int n, const void *d_state, qaoa_state_type st, const void *d_costs,
+                         qaoa_cost_type ct, const qaoa_cost_stats *stats, void *d_work,
+                         size_t work_bytes, double *d_out, qaoa_stream_t stream) {
+  qaoa_status r = check_common(n, d_costs, ct, d_state, st);
+  if (r != QAOA_OK) return r;
+  if (!d_out || !stats) return fail(QAOA_ERR_INVALID_ARG, "NULL d_out or stats");
+  Ws ws;
+  r = get_ws(n, d_work, work_bytes, ws);
+  if (r != QAOA_OK) return r;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
+  CK(launch_expect(n, d_state, st == QAOA_C128, d_costs, cost_kind(ct), stats->f_min, ws.partials,
+                   ws.counter, d_out, 1, s, num_sms()),
+     "overlap launch");
+  return QAOA_OK;
+}
+
+qaoa_status qaoa_grad(int n, const void *d_costs, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                      const double *gammas, const double *betas, int p, void *d_state, void *d_lambda,
+                      qaoa_state_type st, void *d_work, size_t work_bytes, double *d_out,
+                      qaoa_stream_t stream) {
+  qaoa_status r = check_common(n, d_costs, ct, d_state, st);
+  if (r != QAOA_OK) return r;
+  if (!aligned16(d_lambda)) return fail(QAOA_ERR_INVALID_ARG, "lambda pointer NULL or not 16-byte aligned");
+  if (!stats || !d_out || ((uintptr_t)d_out & 7u)) return fail(QAOA_ERR_INVALID_ARG, "NULL stats or bad d_out");
+  r = check_angles(gammas, betas, p);
+  if (r != QAOA_OK) return r;
+  Ws ws;
+  r = get_ws(n, d_work, work_bytes, ws);
+  if (r != QAOA_OK) return r;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n <= kSmallMaxN) {
+    return st == QAOA_C64
+               ? small_grad<float>(n, d_costs, ct, stats->f_min, gammas, betas, p, d_state, d_lambda, d_out, s)
+               : small_grad<double>(n, d_costs, ct, stats->f_min, gammas, betas, p, d_state, d_lambda, d_out, s);
+  }
+  CK(cudaMemsetAsync(d_out + 2, 0, sizeof(double) * 2 * (size_t)p, s), "memset grad");
+  r = st == QAOA_C64
+          ? tiled_forward<float>(n, d_costs, ct, stats, gammas, betas, p, d_state, 1, ws, d_out, s)
+          : tiled_forward<double>(n, d_costs, ct, stats, gammas, betas, p, d_state, 1, ws, d_out, s);
+  if (r != QAOA_OK) return r;
+  return st == QAOA_C64
+             ? tiled_backward<float>(n, d_costs, ct, stats, gammas, betas, p, d_state, d_lambda, ws,
+                                     d_out + 2, d_out + 2 + p, s)
+             : tiled_backward<double>(n, d_costs, ct, stats, gammas, betas, p, d_state, d_lambda, ws,
+                                      d_out + 2, d_out + 2 + p, s);
+}
+
+}  // extern "C"

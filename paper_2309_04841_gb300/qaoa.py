@@ -1,0 +1,315 @@
+"""Thin Python binding of libqaoa.so (include/qaoa.h), same names as the C ABI.
+
+Argument marshalling only: torch tensors provide device memory and the
+current CUDA stream, every step of the computation runs in the library's
+kernels.  There is no CPU fallback: if the library cannot be loaded the call
+raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqaoa.so")
+
+COST_I32, COST_F32, COST_F64 = 0, 1, 2
+C64, C128 = 0, 1
+
+TERM_DTYPE = np.dtype([("weight", np.float64), ("mask", np.uint64)])
+
+_STATUS = {0: "ok", 1: "invalid argument", 2: "buffer too small", 3: "integer cost overflow",
+           4: "CUDA error", 5: "timeout", 6: "rejected", 7: "cancelled", 8: "not found",
+           9: "busy"}
+
+
+class QAOAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CostStats(C.Structure):
+    _fields_ = [("f_min", C.c_double), ("f_max", C.c_double), ("n_min", C.c_uint64)]
+
+    def __repr__(self):
+        return f"CostStats(f_min={self.f_min}, f_max={self.f_max}, n_min={self.n_min})"
+
+
+_lib = None
+
+
+def lib():
+    """Load libqaoa.so (building it first if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            from . import build as _build
+            _build.build()
+        L = C.CDLL(LIB_PATH)
+        P, I, Z, D = C.c_void_p, C.c_int, C.c_size_t, C.c_double
+        sig = {
+            "qaoa_status_string": ([I], C.c_char_p),
+            "qaoa_last_error_message": ([], C.c_char_p),
+            "qaoa_version": ([], I),
+            "qaoa_workspace_bytes": ([I], Z),
+            "qaoa_labs_terms": ([I, P, Z, P], I),
+            "qaoa_maxcut_terms": ([I, P, P, Z, P, Z, P], I),
+            "qaoa_precompute_costs": ([I, P, Z, I, P, P], I),
+            "qaoa_labs_costs": ([I, P, P], I),
+            "qaoa_maxcut_costs": ([I, P, P, Z, I, P, P], I),
+            "qaoa_cost_stats_compute": ([I, P, I, P, Z, P, P], I),
+            "qaoa_simulate": ([I, P, I, P, P, P, I, P, I, I, P, Z, P, P], I),
+            "qaoa_expectation": ([I, P, I, P, I, P, Z, P, P], I),
+            "qaoa_overlap": ([I, P, I, P, I, P, P, Z, P, P], I),
+            "qaoa_grad": ([I, P, I, P, P, P, I, P, P, I, P, Z, P, P], I),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        raise QAOAError(st, lib().qaoa_last_error_message().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    torch = _torch()
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def cost_dtype(ct):
+    torch = _torch()
+    return {COST_I32: torch.int32, COST_F32: torch.float32, COST_F64: torch.float64}[ct]
+
+
+def state_dtype(st):
+    torch = _torch()
+    return {C64: torch.complex64, C128: torch.complex128}[st]
+
+
+def cost_type_of(costs):
+    torch = _torch()
+    return {torch.int32: COST_I32, torch.float32: COST_F32, torch.float64: COST_F64}[costs.dtype]
+
+
+def state_type_of(state):
+    torch = _torch()
+    return {torch.complex64: C64, torch.complex128: C128}[state.dtype]
+
+
+def _n_of(t):
+    n = int(t.numel()).bit_length() - 1
+    if t.numel() != 1 << n:
+        raise ValueError("vector length must be a power of two")
+    return n
+
+
+# ----------------------------------------------------------- host helpers
+
+def terms_array(terms):
+    """[(w, (i, j, ...)), ...] -> qaoa_term array (weight, bit mask)."""
+    a = np.zeros(len(terms), dtype=TERM_DTYPE)
+    for k, (w, idx) in enumerate(terms):
+        a[k]["weight"] = float(w)
+        a[k]["mask"] = np.uint64(sum(1 << int(i) for i in idx))
+    return a
+
+
+def labs_terms(n):
+    L = lib()
+    cnt = C.c_size_t(0)
+    st = L.qaoa_labs_terms(n, None, 0, C.byref(cnt))
+    if st not in (0, 2):
+        _check(st)
+    out = np.zeros(cnt.value, dtype=TERM_DTYPE)
+    _check(L.qaoa_labs_terms(n, _np_ptr(out), len(out), C.byref(cnt)))
+    return out
+
+
+def maxcut_terms(n, edges, weights=None):
+    L = lib()
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    w = None if weights is None else np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    out = np.zeros(len(e) + 1, dtype=TERM_DTYPE)
+    cnt = C.c_size_t(0)
+    _check(L.qaoa_maxcut_terms(n, _np_ptr(e), None if w is None else _np_ptr(w), len(e),
+                               _np_ptr(out), len(out), C.byref(cnt)))
+    return out
+
+
+# ------------------------------------------------------------ cost vector
+
+def workspace_bytes(n):
+    return int(lib().qaoa_workspace_bytes(n))
+
+
+def workspace(n, device="cuda"):
+    torch = _torch()
+    return torch.empty(workspace_bytes(n), dtype=torch.uint8, device=device)
+
+
+def precompute_costs(n, terms, cost_type=COST_I32, out=None):
+    torch = _torch()
+    t = terms if isinstance(terms, np.ndarray) and terms.dtype == TERM_DTYPE else terms_array(terms)
+    t = np.ascontiguousarray(t)
+    if out is None:
+        out = torch.empty(1 << n, dtype=cost_dtype(cost_type), device="cuda")
+    _check(lib().qaoa_precompute_costs(n, _np_ptr(t) if len(t) else None, len(t), cost_type,
+                                       _ptr(out), _stream()))
+    return out
+
+
+def labs_costs(n, out=None):
+    torch = _torch()
+    if out is None:
+        out = torch.empty(1 << n, dtype=torch.int32, device="cuda")
+    _check(lib().qaoa_labs_costs(n, _ptr(out), _stream()))
+    return out
+
+
+def maxcut_costs(n, edges, weights=None, cost_type=COST_I32, out=None):
+    torch = _torch()
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    w = None if weights is None else np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    if out is None:
+        out = torch.empty(1 << n, dtype=cost_dtype(cost_type), device="cuda")
+    _check(lib().qaoa_maxcut_costs(n, _np_ptr(e), None if w is None else _np_ptr(w), len(e),
+                                   cost_type, _ptr(out), _stream()))
+    return out
+
+
+def cost_stats_compute(costs, work=None):
+    n = _n_of(costs)
+    if work is None:
+        work = workspace(n)
+    st = CostStats()
+    _check(lib().qaoa_cost_stats_compute(n, _ptr(costs), cost_type_of(costs), _ptr(work),
+                                         work.numel(), C.byref(st), _stream()))
+    return st
+
+
+# ------------------------------------------------------------- simulation
+
+def _angles(gammas, betas):
+    g = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64).reshape(-1))
+    b = np.ascontiguousarray(np.asarray(betas, dtype=np.float64).reshape(-1))
+    if len(g) != len(b):
+        raise ValueError("gammas and betas must have the same length")
+    return g, b
+
+
+def simulate(costs, stats, gammas, betas, state=None, state_type=C64, init_plus=True,
+             work=None, out=None, reduce=True):
+    """Algorithm 3 on the device.  Returns (state, out) where out holds
+    [E, O] (device float64) when reduce is True, else None."""
+    torch = _torch()
+    n = _n_of(costs)
+    g, b = _angles(gammas, betas)
+    if state is None:
+        state = torch.empty(1 << n, dtype=state_dtype(state_type), device="cuda")
+        init_plus = True
+    if work is None:
+        work = workspace(n)
+    if reduce and out is None:
+        out = torch.empty(2, dtype=torch.float64, device="cuda")
+    _check(lib().qaoa_simulate(n, _ptr(costs), cost_type_of(costs), C.byref(stats), _np_ptr(g),
+                               _np_ptr(b), len(g), _ptr(state), state_type_of(state),
+                               1 if init_plus else 0, _ptr(work), work.numel(),
+                               _ptr(out) if reduce else None, _stream()))
+    return state, (out if reduce else None)
+
+
+def expectation(state, costs, work=None, out=None):
+    torch = _torch()
+    n = _n_of(costs)
+    if work is None:
+        work = workspace(n)
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+    _check(lib().qaoa_expectation(n, _ptr(state), state_type_of(state), _ptr(costs),
+                                  cost_type_of(costs), _ptr(work), work.numel(), _ptr(out),
+                                  _stream()))
+    return out
+
+
+def overlap(state, costs, stats, work=None, out=None):
+    torch = _torch()
+    n = _n_of(costs)
+    if work is None:
+        work = workspace(n)
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+    _check(lib().qaoa_overlap(n, _ptr(state), state_type_of(state), _ptr(costs),
+                              cost_type_of(costs), C.byref(stats), _ptr(work), work.numel(),
+                              _ptr(out), _stream()))
+    return out
+
+
+def grad(costs, stats, gammas, betas, state=None, lam=None, state_type=C64, work=None, out=None):
+    """Objective and adjoint gradient.  Returns the device float64 tensor
+    [E, O, dE/dgamma_1..p, dE/dbeta_1..p]."""
+    torch = _torch()
+    n = _n_of(costs)
+    g, b = _angles(gammas, betas)
+    p = len(g)
+    if state is None:
+        state = torch.empty(1 << n, dtype=state_dtype(state_type), device="cuda")
+    if lam is None:
+        lam = torch.empty_like(state)
+    if work is None:
+        work = workspace(n)
+    if out is None:
+        out = torch.empty(2 + 2 * p, dtype=torch.float64, device="cuda")
+    _check(lib().qaoa_grad(n, _ptr(costs), cost_type_of(costs), C.byref(stats), _np_ptr(g),
+                           _np_ptr(b), p, _ptr(state), _ptr(lam), state_type_of(state),
+                           _ptr(work), work.numel(), _ptr(out), _stream()))
+    return out
+
+
+class _EnergyFn:
+    """Factory for the torch.autograd.Function (built lazily so importing this
+    module does not import torch)."""
+    fn = None
+
+
+def qaoa_energy(costs, stats, gammas, betas, state_type=C64):
+    """E(gammas, betas) as a differentiable torch scalar: forward and backward
+    both run through qaoa_grad (one forward + one adjoint sweep)."""
+    torch = _torch()
+    if _EnergyFn.fn is None:
+        class QAOAEnergy(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, g, b, costs, stats, st):
+                out = grad(costs, stats, g.detach().cpu().numpy(), b.detach().cpu().numpy(),
+                           state_type=st)
+                p = g.numel()
+                dg = out[2:2 + p].to(device=g.device, dtype=g.dtype)
+                db = out[2 + p:].to(device=b.device, dtype=b.dtype)
+                ctx.save_for_backward(dg.reshape(g.shape), db.reshape(b.shape))
+                return out[0].to(device=g.device, dtype=g.dtype)
+
+            @staticmethod
+            def backward(ctx, gy):
+                dg, db = ctx.saved_tensors
+                return gy * dg, gy * db, None, None, None
+
+        _EnergyFn.fn = QAOAEnergy
+    return _EnergyFn.fn.apply(gammas, betas, costs, stats, state_type)

@@ -1,0 +1,201 @@
+"""Forward simulation (Algorithm 3), energy and overlap on the GPU vs the
+oracle, element by element.
+
+Tolerances.  complex64 runs FP32 rotations (unit roundoff u = 6e-8) with
+the phase argument reduced in extended precision, so after L layers of n
+rotations the state error is a few u * sqrt(n L) in norm: ||d psi|| / ||psi||
+<= 2e-5 covers n L <= 10^4 with margin, and energies are held to 1e-5
+relative.  complex128 is held to 1e-11 (state) and 1e-10 (energy)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_04841_gb300 import inputs as I
+
+from gpu_util import dev_np, fidelity, gpu_costs, oracle_costs, rel_state_err, torch
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+TOL = {"c64": dict(state=2e-5, energy=1e-5), "c128": dict(state=1e-11, energy=1e-10)}
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_2309_04841_gb300 import qaoa
+    qaoa.lib()
+    return qaoa
+
+
+def st_type(Q, s):
+    return Q.C64 if s == "c64" else Q.C128
+
+
+def run_case(Q, n, f_np, f_dev, g, b, st, psi0=None):
+    T = torch()
+    stats = Q.cost_stats_compute(f_dev)
+    if psi0 is None:
+        state, out = Q.simulate(f_dev, stats, g, b, state_type=st_type(Q, st))
+    else:
+        dt = T.complex64 if st == "c64" else T.complex128
+        state = T.as_tensor(psi0.astype(np.complex64 if st == "c64" else np.complex128)).to("cuda")
+        state, out = Q.simulate(f_dev, stats, g, b, state=state, init_plus=False)
+    ref = oracle.simulate(n, f_np, g, b, psi0=psi0)
+    got = dev_np(state)
+    o = dev_np(out)
+    E, O = oracle.energy(n, ref, f_np), oracle.overlap(n, ref, f_np)
+    return got, ref, o, E, O
+
+
+@pytest.mark.parametrize("st", ["c64", "c128"])
+@pytest.mark.parametrize("n", list(range(2, 21)) + [22, 23, 24])
+def test_labs_forward_all_n(Q, n, st):
+    # every n: the on-chip path (n <= 12), the single-tile boundary (13) and
+    # the LOW/HIGH pass splits with ragged last groups (14..24)
+    p = 3
+    g = I.angles(p, 100 + n, 0, 0.2)
+    b = I.angles(p, 200 + n)
+    f = oracle.labs_costs(n)
+    got, ref, o, E, O = run_case(Q, n, f.astype(float), Q.labs_costs(n), g, b, st)
+    assert rel_state_err(got, ref) < TOL[st]["state"]
+    assert abs(o[0] - E) <= TOL[st]["energy"] * abs(E)
+    assert abs(o[1] - O) <= TOL[st]["energy"] * max(O, 1e-300) + 1e-14
+
+
+@pytest.mark.parametrize("st", ["c64", "c128"])
+@pytest.mark.parametrize("n", [9, 13, 17, 21])
+def test_random_input_state(Q, n, st):
+    # a random (non-uniform) input state exercises every pass without the
+    # symmetry of |+>; real float32 costs take the computed-phase path
+    p = 2
+    edges, w = I.maxcut_3reg(n + (n % 2), graph_seed=n, weighted=True, weight_seed=3)
+    m = n + (n % 2)
+    terms = I.random_terms(n, 30, n, max_order=3, integer=False)
+    f = oracle.to_f32_rne(oracle.costs_terms_real(n, terms))
+    fd = Q.precompute_costs(n, terms, Q.COST_F32)
+    psi0 = I.random_state(n, 1000 + n)
+    g = I.angles(p, 300 + n, 0, 1.0)
+    b = I.angles(p, 400 + n)
+    got, ref, o, E, O = run_case(Q, n, f.astype(float), fd, g, b, st, psi0=psi0)
+    assert rel_state_err(got, ref) < TOL[st]["state"]
+    assert abs(o[0] - E) <= TOL[st]["energy"] * abs(E) + 1e-7
+    del edges, w, m
+
+
+@pytest.mark.parametrize("n", [12, 16])
+def test_large_range_integer_costs_use_computed_phase(Q, n):
+    # integer costs whose range exceeds the two-level phase table
+    terms = [(30000, (0, 1)), (25000, (2,)), (7, (3, 4, 5))]
+    f = oracle.costs_terms_int(n, terms)
+    assert f.max() - f.min() >= 65536
+    fd = Q.precompute_costs(n, terms, Q.COST_I32)
+    g = [0.013, 0.002]
+    b = [0.4, 1.1]
+    for st in ("c64", "c128"):
+        got, ref, o, E, O = run_case(Q, n, f.astype(float), fd, g, b, st)
+        assert rel_state_err(got, ref) < TOL[st]["state"]
+
+
+@pytest.mark.parametrize("n", [10, 15])
+def test_trivial_angles(Q, n):
+    # gamma = beta = 0: E = mean(f), O = #argmin / 2^n
+    f = oracle.labs_costs(n)
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    for g, b in [([0.0], [0.0]), ([0.7, 0.3], [0.0, 0.0]), ([0.0], [0.9])]:
+        _, out = Q.simulate(fd, stats, g, b)
+        o = dev_np(out)
+        assert abs(o[0] - f.mean()) <= 1e-6 * f.mean()
+        assert abs(o[1] - np.sum(f == f.min()) / 2 ** n) <= 1e-6 * np.sum(f == f.min()) / 2 ** n
+
+
+def test_many_layers_norm_and_chunking(Q):
+    # p > 128 crosses the on-chip kernel's layer chunk; the norm stays 1
+    for n in (8, 14):
+        f = oracle.labs_costs(n)
+        fd = Q.labs_costs(n)
+        stats = Q.cost_stats_compute(fd)
+        p = 300
+        g = I.angles(p, 5, 0, 0.05)
+        b = I.angles(p, 6)
+        state, out = Q.simulate(fd, stats, g, b, state_type=Q.C128)
+        ref = oracle.simulate(n, f.astype(float), g, b)
+        assert rel_state_err(dev_np(state), ref) < 1e-10
+        state, out = Q.simulate(fd, stats, g, b, state_type=Q.C64)
+        s = dev_np(state).astype(np.complex128)
+        assert abs(np.vdot(s, s).real - 1) < 1e-4
+        assert fidelity(s, ref) > 1 - 1e-6
+
+
+def test_standalone_expectation_and_overlap(Q):
+    T = torch()
+    for n in (11, 19):
+        psi0 = I.random_state(n, 7 + n)
+        f = oracle.labs_costs(n)
+        fd = Q.labs_costs(n)
+        stats = Q.cost_stats_compute(fd)
+        for dt in (T.complex64, T.complex128):
+            s = T.as_tensor(psi0).to(dt).to("cuda")
+            ref = psi0.astype(np.complex64).astype(np.complex128) if dt == T.complex64 else psi0
+            e = dev_np(Q.expectation(s, fd))[0]
+            o = dev_np(Q.overlap(s, fd, stats))[0]
+            assert abs(e - oracle.energy(n, ref, f.astype(float))) < 1e-12 * abs(e)
+            assert abs(o - oracle.overlap(n, ref, f.astype(float))) < 1e-12
+
+
+def test_deterministic_repeat(Q):
+    n = 18
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g = I.angles(4, 1, 0, 0.1)
+    b = I.angles(4, 2)
+    a = dev_np(Q.simulate(fd, stats, g, b)[1])
+    c = dev_np(Q.simulate(fd, stats, g, b)[1])
+    assert a.tobytes() == c.tobytes()
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, f"oracle_{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("name,st", [("maxcut3_n14_p2", "c128"), ("maxcut3_n14_p2", "c64"),
+                                     ("maxcut_gnp26_p6", "c64"), ("maxcut_gnp26_p6", "c128")])
+def test_workload_energy_vs_stored_oracle(Q, name, st):
+    G = _golden(name)
+    w = I.workload(name)
+    fd = gpu_costs(w)
+    stats = Q.cost_stats_compute(fd)
+    assert stats.f_min == G["f_min"] and stats.n_min == G["n_min"] and stats.f_max == G["f_max"]
+    g, b = I.workload_angles(w)
+    _, out = Q.simulate(fd, stats, g, b, state_type=st_type(Q, st))
+    o = dev_np(out)
+    assert abs(o[0] - G["energy"]) <= TOL[st]["energy"] * abs(G["energy"])
+    assert abs(o[1] - G["overlap"]) <= TOL[st]["energy"] * G["overlap"] + 1e-15
+
+
+@pytest.mark.parametrize("name", ["labs30_p10", "labs30_p10_smallgamma"])
+def test_labs30_energy_vs_stored_oracle(Q, name):
+    # the headline workload at full size (n = 30, complex64, 8 GB state)
+    G = _golden(name)
+    w = I.workload(name)
+    fd = Q.labs_costs(w["n"])
+    stats = Q.cost_stats_compute(fd)
+    assert (stats.f_min, stats.n_min) == (G["f_min"], G["n_min"])
+    g, b = I.workload_angles(w)
+    state, out = Q.simulate(fd, stats, g, b, state_type=Q.C64)
+    o = dev_np(out)
+    assert abs(o[0] - G["energy"]) <= 1e-5 * abs(G["energy"])
+    assert abs(o[1] - G["overlap"]) <= 1e-4 * G["overlap"] + 1e-12
+    T = torch()
+    nrm = float(T.linalg.vector_norm(state.to(T.complex128)).item())
+    assert abs(nrm - 1) < 1e-5
+    del state
+    T.cuda.empty_cache()

@@ -1,0 +1,125 @@
+"""Adjoint gradient on the GPU vs the oracle's stored-state reverse mode
+(n <= 16) and vs central differences of the GPU's own complex128 forward at
+full size (a property that holds at any n).
+
+Tolerance: the gradient is compared norm-wise, ||g - g_ref|| / ||g_ref||,
+because single components can vanish by symmetry.  complex64 accumulates
+FP32 rounding through 2p(n+1) passes of the forward and adjoint sweeps;
+1e-4 covers p <= 40 with margin.  complex128: 1e-9."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_04841_gb300 import inputs as I
+
+from gpu_util import dev_np, gpu_costs, oracle_costs, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_2309_04841_gb300 import qaoa
+    qaoa.lib()
+    return qaoa
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.mark.parametrize("st,tol", [("c64", 1e-4), ("c128", 1e-9)])
+@pytest.mark.parametrize("n,p", [(3, 2), (8, 4), (12, 3), (13, 2), (14, 3), (16, 4)])
+def test_grad_vs_oracle_labs(Q, n, p, st, tol):
+    f = oracle.labs_costs(n).astype(float)
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g = I.angles(p, 10 + n, 0, 0.1)
+    b = I.angles(p, 20 + n)
+    out = dev_np(Q.grad(fd, stats, g, b, state_type=Q.C64 if st == "c64" else Q.C128))
+    E, dg, db = oracle.grad(n, f, g, b)
+    assert abs(out[0] - E) <= (1e-5 if st == "c64" else 1e-10) * abs(E)
+    assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < tol
+
+
+@pytest.mark.parametrize("n,p", [(10, 5), (16, 6)])
+def test_grad_vs_oracle_weighted_maxcut(Q, n, p):
+    w = I.workload("maxcut3w28_p40", n=n)
+    f, _ = oracle_costs(w)
+    fd = gpu_costs(w)
+    stats = Q.cost_stats_compute(fd)
+    g = I.angles(p, 31, 0, 0.3)
+    b = I.angles(p, 32)
+    out = dev_np(Q.grad(fd, stats, g, b))
+    E, dg, db = oracle.grad(n, f, g, b)
+    assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < 1e-4
+
+
+def test_grad_many_layers_small_chunked(Q):
+    # p > 128 on the on-chip path: forward chunks then adjoint chunks
+    n, p = 7, 150
+    f = oracle.labs_costs(n).astype(float)
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g = I.angles(p, 41, 0, 0.05)
+    b = I.angles(p, 42)
+    out = dev_np(Q.grad(fd, stats, g, b, state_type=Q.C128))
+    E, dg, db = oracle.grad(n, f, g, b)
+    assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < 1e-9
+
+
+def test_grad_uncompute_returns_plus(Q):
+    # after the adjoint sweep psi is back at |+> (layers un-applied in place)
+    T = torch()
+    n, p = 18, 3
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    state = T.empty(1 << n, dtype=T.complex64, device="cuda")
+    Q.grad(fd, stats, I.angles(p, 1, 0, 0.1), I.angles(p, 2), state=state)
+    s = dev_np(state).astype(np.complex128)
+    assert np.max(np.abs(s - 2.0 ** (-n / 2))) < 1e-5 * 2.0 ** (-n / 2) * 10
+
+
+@pytest.mark.parametrize("name", ["labs28_p40", "maxcut3w28_p40"])
+def test_grad_fullsize_directional_fd(Q, name):
+    # n = 28, p = 40, all 80 gradients in one adjoint sweep; checked by a
+    # central difference of the complex128 forward along a random direction
+    w = I.workload(name)
+    fd = gpu_costs(w)
+    stats = Q.cost_stats_compute(fd)
+    g, b = I.angles(w["p"], w["gamma_seed"], 0, w["ghi"]), I.angles(w["p"], w["beta_seed"])
+    T = torch()
+    out = dev_np(Q.grad(fd, stats, g, b))
+    p = w["p"]
+    grad = np.concatenate([out[2:2 + p], out[2 + p:]])
+    v = I.uniform(99, 2 * p, -1, 1)
+    v /= np.linalg.norm(v)
+    fmax = max(abs(stats.f_min), abs(stats.f_max))
+    h = 1e-4 / max(1.0, fmax / 10)
+
+    def E(t):
+        st, o = Q.simulate(fd, stats, g + t * v[:p], b + t * v[p:], state_type=Q.C128)
+        e = float(dev_np(o)[0])
+        del st
+        return e
+
+    fd1 = (E(h) - E(-h)) / (2 * h)
+    fd2 = (E(h / 2) - E(-h / 2)) / h
+    dd = (4 * fd2 - fd1) / 3
+    T.cuda.empty_cache()
+    assert abs(np.dot(grad, v) - dd) <= 1e-4 * np.linalg.norm(grad)
+
+
+def test_autograd_function(Q):
+    T = torch()
+    n, p = 10, 3
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g = T.tensor(I.angles(p, 3, 0, 0.1), dtype=T.float64, requires_grad=True)
+    b = T.tensor(I.angles(p, 4), dtype=T.float64, requires_grad=True)
+    E = Q.qaoa_energy(fd, stats, g, b, state_type=Q.C128)
+    E.backward()
+    f = oracle.labs_costs(n).astype(float)
+    E0, dg, db = oracle.grad(n, f, g.detach().numpy(), b.detach().numpy())
+    assert abs(E.item() - E0) < 1e-10 * abs(E0)
+    assert rel(np.concatenate([g.grad.numpy(), b.grad.numpy()]), np.concatenate([dg, db])) < 1e-9
