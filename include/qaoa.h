@@ -164,6 +164,16 @@ qaoa_status qaoa_cost_stats_compute(int n, const void *d_costs,
  */
 size_t qaoa_workspace_bytes(int n);
 
+/*
+ * Waits for `stream`, then reports whether a kernel that used this workspace
+ * since the last qaoa_simulate / qaoa_grad call started gave up on a bounded
+ * device-side wait (QAOA_ERR_TIMEOUT; the flag is then cleared).  Kernels
+ * never trap or hang: a wait that runs out (about one second) records the
+ * flag and the kernel returns, leaving its outputs incomplete.
+ * Synchronises `stream`.
+ */
+qaoa_status qaoa_workspace_check(void *d_work, size_t work_bytes, qaoa_stream_t stream);
+
 /* ---------------------------------------------------- a2-a4: simulation */
 
 /*
@@ -230,6 +240,33 @@ qaoa_status qaoa_grad(int n, const void *d_costs, qaoa_cost_type ct,
                       const double *betas, int p, void *d_state,
                       void *d_lambda, qaoa_state_type st, void *d_work,
                       size_t work_bytes, double *d_out, qaoa_stream_t stream);
+
+/* ------------------------------------------------------------ profiling */
+
+/* Per-kernel-kind launch statistics (not in the paper; measurement aid). */
+typedef struct {
+    char name[24];      /* kernel kind, e.g. "fwd_low", "bwd_high"          */
+    uint64_t launches;  /* launches recorded since the last reset            */
+    double ms;          /* summed device time between the bracketing events  */
+    double bytes;       /* summed algorithmic HBM bytes of those launches:
+                           every state vector read and written once, the cost
+                           vector read once where the launch needs it        */
+} qaoa_prof_entry;
+
+/*
+ * When `on` is nonzero every kernel launch of this library is bracketed by
+ * two CUDA events recorded on the launching stream (events come from a pool
+ * created here; up to 65536 launches are recorded, later ones are counted
+ * but not timed).  Turning it off keeps the records for qaoa_profile_read.
+ */
+qaoa_status qaoa_profile_enable(int on);
+
+/*
+ * Aggregates the recorded launches per kernel kind into out[0..cap) (host),
+ * sets *n_out to the number of kinds, and if reset != 0 clears the records.
+ * Waits for the recorded events (synchronises with the launches).
+ */
+qaoa_status qaoa_profile_read(qaoa_prof_entry *out, int cap, int *n_out, int reset);
 
 #ifdef __cplusplus
 }

@@ -36,10 +36,20 @@ qaoa_status cuda_fail(cudaError_t e, const char *where) {
   return QAOA_ERR_CUDA;
 }
 
-#define CK(expr, where)                       \
-  do {                                        \
-    cudaError_t _e = (expr);                  \
+#define CK(expr, where)                                 \
+  do {                                                  \
+    cudaError_t _e = (expr);                            \
     if (_e != cudaSuccess) return cuda_fail(_e, where); \
+  } while (0)
+
+// Launch `call` on stream `st`, bracketed by profiling events when enabled;
+// `bytes` is the launch's algorithmic HBM traffic.
+#define LAUNCH(kind, bytes, st, call)                          \
+  do {                                                         \
+    const int _pid = prof_begin(st);                           \
+    cudaError_t _e = (call);                                   \
+    prof_end(_pid, st, kind, (double)(bytes));                 \
+    if (_e != cudaSuccess) return cuda_fail(_e, kind " launch"); \
   } while (0)
 
 int num_sms() {
@@ -75,6 +85,7 @@ size_t partial_doubles(int n) {
 
 struct Ws {
   unsigned *counter;
+  unsigned *err;  // set to nonzero by a kernel whose bounded wait ran out
   double *small;
   double *partials;
 };
@@ -84,6 +95,7 @@ qaoa_status get_ws(int n, void *d_work, size_t bytes, Ws &ws) {
   if (bytes < qaoa_workspace_bytes(n)) return fail(QAOA_ERR_OUT_OF_MEMORY, "workspace smaller than qaoa_workspace_bytes(n)");
   char *b = reinterpret_cast<char *>(d_work);
   ws.counter = reinterpret_cast<unsigned *>(b + kWsCounters);
+  ws.err = reinterpret_cast<unsigned *>(b + kWsCounters + 64);
   ws.small = reinterpret_cast<double *>(b + kWsSmall);
   ws.partials = reinterpret_cast<double *>(b + kWsPartials);
   return QAOA_OK;
@@ -196,6 +208,8 @@ SmallLayer<Real> small_layer(double gamma, double beta) {
 
 int cost_kind(qaoa_cost_type ct) { return (int)ct; }
 
+double cost_bytes(qaoa_cost_type ct) { return ct == QAOA_COST_F64 ? 8.0 : 4.0; }
+
 // ----------------------------------------------------------- small path
 
 template <typename Real>
@@ -220,7 +234,7 @@ qaoa_status small_forward(int n, const void *cost, qaoa_cost_type ct, double fmi
     P.fmin_d = fmin;
     P.out = d_out;
     for (int i = 0; i < nl; ++i) P.L[i] = small_layer<Real>(gam[l0 + i], bet[l0 + i]);
-    CK(launch_small(P, s), "small forward launch");
+    LAUNCH("small", 2.0 * sizeof(C2) * (double)(1 << n), s, launch_small(P, s));
   }
   return QAOA_OK;
 }
@@ -249,7 +263,7 @@ qaoa_status small_grad(int n, const void *cost, qaoa_cost_type ct, double fmin, 
     P.out_dg = d_out + 2;
     P.out_db = d_out + 2 + p;
     for (int i = 0; i < p; ++i) P.L[i] = small_layer<Real>(gam[i], bet[i]);
-    CK(launch_small(P, s), "small grad launch");
+    LAUNCH("small", 3.0 * sizeof(C2) * (double)(1 << n), s, launch_small(P, s));
     return QAOA_OK;
   }
   qaoa_status st = small_forward<Real>(n, cost, ct, fmin, gam, bet, p, state, 1, d_out, s);
@@ -273,7 +287,7 @@ qaoa_status small_grad(int n, const void *cost, qaoa_cost_type ct, double fmin, 
     P.out_dg = d_out + 2 + l0;
     P.out_db = d_out + 2 + p + l0;
     for (int i = 0; i < nl; ++i) P.L[i] = small_layer<Real>(gam[l0 + i], bet[l0 + i]);
-    CK(launch_small(P, s), "small adjoint launch");
+    LAUNCH("small", 4.0 * sizeof(C2) * (double)(1 << n), s, launch_small(P, s));
   }
   return QAOA_OK;
 }
@@ -287,6 +301,65 @@ template <typename Real> struct BwdTB;
 template <> struct BwdTB<float> { using Low = PlanT12Low; using High = PlanT12High; };
 template <> struct BwdTB<double> { using Low = PlanT11Low; using High = PlanT11High; };
 
+// One pass of a schedule: [sweep s1 of group g with beta_{l1}] [phase of layer lp]
+// [sweep s2 of group g with beta_{l2}]; -1 marks an absent part.
+struct PassOp {
+  int group;
+  int l1, lp, l2;
+  bool init;    // forward: start from |+>;  adjoint: lambda <- f psi
+  bool reduce;  // forward: energy/overlap of the result
+};
+
+// Forward schedule with cross-layer fusion.  Layer l applies every group
+// once; the X rotations of different qubits commute, so each layer's group
+// order is free.  Taking layer l+1's order as the reverse of layer l's, the
+// last group of layer l is the first of layer l+1, and both share one pass
+// around the phase of layer l+1: p*k - (p-1) passes instead of p*k.
+std::vector<PassOp> forward_schedule(int k, int p, bool init_plus, bool reduce) {
+  std::vector<PassOp> ops;
+  if (k == 1) {
+    for (int l = 0; l < p; ++l) ops.push_back(PassOp{0, -1, l, l, l == 0 && init_plus, false});
+  } else {
+    std::vector<int> order(k);
+    for (int i = 0; i < k; ++i) order[i] = i;
+    ops.push_back(PassOp{order[0], -1, 0, 0, init_plus, false});
+    for (int l = 0; l < p; ++l) {
+      for (int i = 1; i + 1 < k; ++i) ops.push_back(PassOp{order[i], -1, -1, l, false, false});
+      const int z = order[k - 1];
+      if (l + 1 < p)
+        ops.push_back(PassOp{z, l, l + 1, l + 1, false, false});
+      else
+        ops.push_back(PassOp{z, l, -1, -1, false, false});
+      std::vector<int> rev(order.rbegin(), order.rend());
+      order = rev;
+    }
+  }
+  ops.back().reduce = reduce;
+  return ops;
+}
+
+// Adjoint schedule: un-apply layers p-1 .. 0.  s1 un-rotates layer l1 (and
+// accumulates its d/d beta), the phase part accumulates d/d gamma of layer lp
+// and un-applies that phase, s2 un-rotates layer l2 < lp.
+std::vector<PassOp> adjoint_schedule(int k, int p) {
+  std::vector<PassOp> ops;
+  if (k == 1) {
+    for (int l = p - 1; l >= 0; --l) ops.push_back(PassOp{0, l, l, -1, l == p - 1, false});
+    return ops;
+  }
+  std::vector<int> order(k);
+  for (int i = 0; i < k; ++i) order[i] = i;
+  for (int l = p - 1; l >= 0; --l) {
+    if (l == p - 1) ops.push_back(PassOp{order[0], l, -1, -1, true, false});
+    for (int i = 1; i + 1 < k; ++i) ops.push_back(PassOp{order[i], l, -1, -1, false, false});
+    const int z = order[k - 1];
+    ops.push_back(PassOp{z, l, l, l > 0 ? l - 1 : -1, false, false});
+    std::vector<int> rev(order.rbegin(), order.rend());
+    order = rev;
+  }
+  return ops;
+}
+
 template <typename Real>
 qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
                           const double *gam, const double *bet, int p, void *state, int init_plus,
@@ -296,32 +369,44 @@ qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa
   using High = typename FwdTB<Real>::High;
   const int TB = Low::TB;
   const std::vector<Group> gs = plan_groups(n, TB);
+  const std::vector<PassOp> ops = forward_schedule((int)gs.size(), p, init_plus != 0, d_out != nullptr);
   const int nsm = num_sms();
   if (d_out) CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
   FwdParams<Real> P;
-  for (int l = 0; l < p; ++l) {
-    for (size_t gi = 0; gi < gs.size(); ++gi) {
-      const Group &G = gs[gi];
-      memset(&P, 0, sizeof(P));
-      P.psi = reinterpret_cast<C2 *>(state);
-      P.cost = cost;
-      P.cost_kind = cost_kind(ct);
-      P.g = make_geom(n, G, TB);
-      P.s1 = Sweep{{0, 0, 0, 0}};
-      P.s2 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
-      P.c2 = (Real)cos(bet[l]);
-      P.s2s = (Real)sin(bet[l]);
-      P.has_phase = (gi == 0);
-      if (P.has_phase) make_phase<Real>(P.ph, gam[l], ct, stats);
-      P.init_plus = (l == 0 && gi == 0 && init_plus);
-      P.amp = (Real)(1.0 / sqrt(ldexp(1.0, n)));
-      P.reduce = (l == p - 1 && gi + 1 == gs.size() && d_out != nullptr);
-      P.fmin_d = stats ? stats->f_min : 0.0;
-      P.partials = ws.partials;
-      P.counter = ws.counter;
-      P.out = d_out;
-      CK(launch_fwd(P, G.high, s, nsm), "forward pass launch");
+  for (const PassOp &op : ops) {
+    const Group &G = gs[op.group];
+    memset(&P, 0, sizeof(P));
+    P.psi = reinterpret_cast<C2 *>(state);
+    P.cost = cost;
+    P.cost_kind = cost_kind(ct);
+    P.g = make_geom(n, G, TB);
+    const bool two = op.l1 >= 0 && op.l2 >= 0;  // both sweeps: s1 ascends, s2 descends
+    if (op.l1 >= 0) {
+      P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
+      P.c1 = (Real)cos(bet[op.l1]);
+      P.s1s = (Real)sin(bet[op.l1]);
     }
+    if (op.l2 >= 0) {
+      P.s2 = G.high ? make_sweep<High>(G.rot, !two) : make_sweep<Low>(G.rot, !two);
+      P.c2 = (Real)cos(bet[op.l2]);
+      P.s2s = (Real)sin(bet[op.l2]);
+    }
+    P.has_phase = op.lp >= 0;
+    if (P.has_phase) make_phase<Real>(P.ph, gam[op.lp], ct, stats);
+    P.init_plus = op.init;
+    P.amp = (Real)(1.0 / sqrt(ldexp(1.0, n)));
+    P.reduce = op.reduce;
+    P.fmin_d = stats ? stats->f_min : 0.0;
+    P.partials = ws.partials;
+    P.counter = ws.counter;
+    P.out = d_out;
+    const double N = (double)(1ull << n);
+    const double bytes = (P.init_plus ? 1.0 : 2.0) * sizeof(C2) * N +
+                         ((P.has_phase || P.reduce) ? cost_bytes(ct) * N : 0.0);
+    if (G.high)
+      LAUNCH("fwd_high", bytes, s, launch_fwd(P, true, s, nsm));
+    else
+      LAUNCH("fwd_low", bytes, s, launch_fwd(P, false, s, nsm));
   }
   return QAOA_OK;
 }
@@ -335,34 +420,152 @@ qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qao
   using High = typename BwdTB<Real>::High;
   const int TB = Low::TB;
   const std::vector<Group> gs = plan_groups(n, TB);
+  const std::vector<PassOp> ops = adjoint_schedule((int)gs.size(), p);
   const int nsm = num_sms();
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
   BwdParams<Real> P;
-  bool first = true;
-  for (int l = p - 1; l >= 0; --l) {
-    for (int gi = (int)gs.size() - 1; gi >= 0; --gi) {
-      const Group &G = gs[gi];
-      memset(&P, 0, sizeof(P));
-      P.psi = reinterpret_cast<C2 *>(state);
-      P.lam = reinterpret_cast<C2 *>(lam);
-      P.cost = cost;
-      P.cost_kind = cost_kind(ct);
-      P.g = make_geom(n, G, TB);
-      P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
-      P.s2 = Sweep{{0, 0, 0, 0}};
-      P.c1 = (Real)cos(bet[l]);
-      P.s1s = (Real)-sin(bet[l]);
-      P.has_phase = (gi == 0);
-      if (P.has_phase) make_phase<Real>(P.ph, -gam[l], ct, stats);
-      P.init_lambda = first;
-      first = false;
-      P.partials = ws.partials;
-      P.counter = ws.counter;
-      P.out_b1 = d_grad_b + l;
-      P.out_g = P.has_phase ? d_grad_g + l : nullptr;
-      P.out_b2 = nullptr;
-      CK(launch_bwd(P, G.high, s, nsm), "adjoint pass launch");
+  for (const PassOp &op : ops) {
+    const Group &G = gs[op.group];
+    memset(&P, 0, sizeof(P));
+    P.psi = reinterpret_cast<C2 *>(state);
+    P.lam = reinterpret_cast<C2 *>(lam);
+    P.cost = cost;
+    P.cost_kind = cost_kind(ct);
+    P.g = make_geom(n, G, TB);
+    P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
+    P.c1 = (Real)cos(bet[op.l1]);
+    P.s1s = (Real)-sin(bet[op.l1]);
+    P.out_b1 = d_grad_b + op.l1;
+    if (op.lp >= 0) {
+      P.has_phase = 1;
+      make_phase<Real>(P.ph, -gam[op.lp], ct, stats);
+      P.out_g = d_grad_g + op.lp;
     }
+    if (op.l2 >= 0) {
+      P.s2 = G.high ? make_sweep<High>(G.rot, false) : make_sweep<Low>(G.rot, false);
+      P.c2 = (Real)cos(bet[op.l2]);
+      P.s2s = (Real)-sin(bet[op.l2]);
+      P.out_b2 = d_grad_b + op.l2;
+    }
+    P.init_lambda = op.init;
+    P.partials = ws.partials;
+    P.counter = ws.counter;
+    const double N = (double)(1ull << n);
+    const double bytes = (P.init_lambda ? 3.0 : 4.0) * sizeof(C2) * N +
+                         ((P.has_phase || P.init_lambda) ? cost_bytes(ct) * N : 0.0);
+    if (G.high)
+      LAUNCH("bwd_high", bytes, s, launch_bwd(P, true, s, nsm));
+    else
+      LAUNCH("bwd_low", bytes, s, launch_bwd(P, false, s, nsm));
+  }
+  return QAOA_OK;
+}
+
+// ---------------------------------------------------- TMA (complex64) path
+
+bool tma_ok(qaoa_cost_type ct) { return ct == QAOA_COST_I32 || ct == QAOA_COST_F32; }
+
+qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                        const double *gam, const double *bet, int p, void *state, int init_plus,
+                        const Ws &ws, double *d_out, cudaStream_t s) {
+  using Low = PlanTmaF13Low;
+  using High = PlanTmaF13High;
+  const int TB = Low::TB;
+  const std::vector<Group> gs = plan_groups(n, TB);
+  const std::vector<PassOp> ops = forward_schedule((int)gs.size(), p, init_plus != 0, d_out != nullptr);
+  const int nsm = num_sms();
+  if (d_out) CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
+  static TmaFwdParams P;  // parameter block; launches copy it, calls are serialised
+  static std::mutex *mu = new std::mutex();
+  std::lock_guard<std::mutex> lock(*mu);
+  for (const PassOp &op : ops) {
+    const Group &G = gs[op.group];
+    memset(&P, 0, sizeof(P));
+    const int h = G.high ? G.h : 4;
+    CK(make_tile_map(&P.map_psi, state, n, TB, h, 8, true), "tensor map (state)");
+    CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, 4, false), "tensor map (cost)");
+    P.ntiles = 1ull << (n - TB);
+    P.h = h;
+    P.cost_kind = cost_kind(ct);
+    const bool two = op.l1 >= 0 && op.l2 >= 0;
+    if (op.l1 >= 0) {
+      P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
+      P.c1 = (float)cos(bet[op.l1]);
+      P.s1s = (float)sin(bet[op.l1]);
+    }
+    if (op.l2 >= 0) {
+      P.s2 = G.high ? make_sweep<High>(G.rot, !two) : make_sweep<Low>(G.rot, !two);
+      P.c2 = (float)cos(bet[op.l2]);
+      P.s2s = (float)sin(bet[op.l2]);
+    }
+    P.has_phase = op.lp >= 0;
+    if (P.has_phase) make_phase<float>(P.ph, gam[op.lp], ct, stats);
+    P.init_plus = op.init;
+    P.amp = (float)(1.0 / sqrt(ldexp(1.0, n)));
+    P.reduce = op.reduce;
+    P.fmin_d = stats ? stats->f_min : 0.0;
+    P.partials = ws.partials;
+    P.counter = ws.counter;
+    P.out = d_out;
+    P.err = ws.err;
+    const double N = (double)(1ull << n);
+    const double bytes = (P.init_plus ? 8.0 : 16.0) * N + ((P.has_phase || P.reduce) ? 4.0 * N : 0.0);
+    if (G.high)
+      LAUNCH("fwd_high", bytes, s, launch_fwd_tma(P, true, s, nsm));
+    else
+      LAUNCH("fwd_low", bytes, s, launch_fwd_tma(P, false, s, nsm));
+  }
+  return QAOA_OK;
+}
+
+qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                         const double *gam, const double *bet, int p, void *state, void *lam,
+                         const Ws &ws, double *d_grad_g, double *d_grad_b, cudaStream_t s) {
+  using Low = PlanTmaB12Low;
+  using High = PlanTmaB12High;
+  const int TB = Low::TB;
+  const std::vector<Group> gs = plan_groups(n, TB);
+  const std::vector<PassOp> ops = adjoint_schedule((int)gs.size(), p);
+  const int nsm = num_sms();
+  CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
+  static TmaBwdParams P;
+  static std::mutex *mu = new std::mutex();
+  std::lock_guard<std::mutex> lock(*mu);
+  for (const PassOp &op : ops) {
+    const Group &G = gs[op.group];
+    memset(&P, 0, sizeof(P));
+    const int h = G.high ? G.h : 4;
+    CK(make_tile_map(&P.map_psi, state, n, TB, h, 8, true), "tensor map (psi)");
+    CK(make_tile_map(&P.map_lam, lam, n, TB, h, 8, true), "tensor map (lambda)");
+    CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, 4, false), "tensor map (cost)");
+    P.ntiles = 1ull << (n - TB);
+    P.h = h;
+    P.cost_kind = cost_kind(ct);
+    P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
+    P.c1 = (float)cos(bet[op.l1]);
+    P.s1s = (float)-sin(bet[op.l1]);
+    P.out_b1 = d_grad_b + op.l1;
+    if (op.lp >= 0) {
+      P.has_phase = 1;
+      make_phase<float>(P.ph, -gam[op.lp], ct, stats);
+      P.out_g = d_grad_g + op.lp;
+    }
+    if (op.l2 >= 0) {
+      P.s2 = G.high ? make_sweep<High>(G.rot, false) : make_sweep<Low>(G.rot, false);
+      P.c2 = (float)cos(bet[op.l2]);
+      P.s2s = (float)-sin(bet[op.l2]);
+      P.out_b2 = d_grad_b + op.l2;
+    }
+    P.init_lambda = op.init;
+    P.partials = ws.partials;
+    P.counter = ws.counter;
+    P.err = ws.err;
+    const double N = (double)(1ull << n);
+    const double bytes = (P.init_lambda ? 24.0 : 32.0) * N + ((P.has_phase || P.init_lambda) ? 4.0 * N : 0.0);
+    if (G.high)
+      LAUNCH("bwd_high", bytes, s, launch_bwd_tma(P, true, s, nsm));
+    else
+      LAUNCH("bwd_low", bytes, s, launch_bwd_tma(P, false, s, nsm));
   }
   return QAOA_OK;
 }
@@ -426,6 +629,20 @@ const char *qaoa_status_string(qaoa_status st) {
 }
 
 const char *qaoa_last_error_message(void) { return g_errmsg; }
+
+qaoa_status qaoa_workspace_check(void *d_work, size_t work_bytes, qaoa_stream_t stream) {
+  if (!d_work || work_bytes < kWsPartials) return fail(QAOA_ERR_INVALID_ARG, "bad workspace");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned h = 0;
+  unsigned *err = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(d_work) + kWsCounters + 64);
+  CK(cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, s), "workspace check copy");
+  CK(cudaStreamSynchronize(s), "workspace check sync");
+  if (h != 0) {
+    CK(cudaMemsetAsync(err, 0, sizeof(unsigned), s), "workspace check clear");
+    return fail(QAOA_ERR_TIMEOUT, "a device-side wait ran out of time");
+  }
+  return QAOA_OK;
+}
 
 int qaoa_version(void) { return 100; }
 
@@ -541,7 +758,8 @@ qaoa_status qaoa_precompute_costs(int n, const qaoa_term *terms, size_t n_terms,
       P.wd[k - k0] = w[k];
       P.wl[k - k0] = (int64_t)(mode == kTermFixed ? ldexp(w[k], e_fix) : w[k]);
     }
-    CK(launch_terms(P, s, nsm), "cost terms launch");
+    LAUNCH("costs_terms", cost_bytes(ct) * (double)(1ull << n) * (c > 0 ? 2.0 : 1.0), s,
+           launch_terms(P, s, nsm));
   }
   return QAOA_OK;
 }
@@ -549,7 +767,8 @@ qaoa_status qaoa_precompute_costs(int n, const qaoa_term *terms, size_t n_terms,
 qaoa_status qaoa_labs_costs(int n, int32_t *d_costs, qaoa_stream_t stream) {
   if (n < 2 || n > 32) return fail(QAOA_ERR_INVALID_ARG, "labs_costs: n must be in [2, 32]");
   if (!aligned16(d_costs)) return fail(QAOA_ERR_INVALID_ARG, "labs_costs: bad pointer");
-  CK(launch_labs(n, d_costs, reinterpret_cast<cudaStream_t>(stream), num_sms()), "labs launch");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  LAUNCH("costs_labs", 4.0 * (double)(1ull << n), s, launch_labs(n, d_costs, s, num_sms()));
   return QAOA_OK;
 }
 
@@ -594,7 +813,8 @@ qaoa_status qaoa_maxcut_costs(int n, const int32_t *edges, const double *w, size
     P.wd[e] = wv[e];
     P.wl[e] = (int64_t)(P.mode == kTermFixed ? ldexp(wv[e], e2) : wv[e]);
   }
-  CK(launch_maxcut(P, reinterpret_cast<cudaStream_t>(stream), num_sms()), "maxcut launch");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  LAUNCH("costs_maxcut", cost_bytes(ct) * (double)(1ull << n), s, launch_maxcut(P, s, num_sms()));
   return QAOA_OK;
 }
 
@@ -607,8 +827,8 @@ qaoa_status qaoa_cost_stats_compute(int n, const void *d_costs, qaoa_cost_type c
   if (st != QAOA_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
-  CK(launch_cost_stats(n, d_costs, cost_kind(ct), ws.partials, ws.counter, ws.small, s, num_sms()),
-     "cost stats launch");
+  LAUNCH("cost_stats", cost_bytes(ct) * (double)(1ull << n), s,
+         launch_cost_stats(n, d_costs, cost_kind(ct), ws.partials, ws.counter, ws.small, s, num_sms()));
   double h[3];
   CK(cudaMemcpyAsync(h, ws.small, sizeof(h), cudaMemcpyDeviceToHost, s), "cost stats copy");
   CK(cudaStreamSynchronize(s), "cost stats sync");
@@ -637,6 +857,9 @@ qaoa_status qaoa_simulate(int n, const void *d_costs, qaoa_cost_type ct, const q
                ? small_forward<float>(n, d_costs, ct, stats->f_min, gammas, betas, p, d_state, init_plus, d_out, s)
                : small_forward<double>(n, d_costs, ct, stats->f_min, gammas, betas, p, d_state, init_plus, d_out, s);
   }
+  CK(cudaMemsetAsync(ws.err, 0, sizeof(unsigned), s), "memset error word");
+  if (st == QAOA_C64 && tma_ok(ct))
+    return tma_forward(n, d_costs, ct, stats, gammas, betas, p, d_state, init_plus, ws, d_out, s);
   return st == QAOA_C64
              ? tiled_forward<float>(n, d_costs, ct, stats, gammas, betas, p, d_state, init_plus, ws, d_out, s)
              : tiled_forward<double>(n, d_costs, ct, stats, gammas, betas, p, d_state, init_plus, ws, d_out, s);
@@ -653,9 +876,9 @@ qaoa_status qaoa_expectation(int n, const void *d_state, qaoa_state_type st, con
   if (r != QAOA_OK) return r;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
-  CK(launch_expect(n, d_state, st == QAOA_C128, d_costs, cost_kind(ct), 0.0, ws.partials, ws.counter,
-                   d_out, 0, s, num_sms()),
-     "expectation launch");
+  LAUNCH("expect", ((st == QAOA_C128 ? 16.0 : 8.0) + cost_bytes(ct)) * (double)(1ull << n), s,
+         launch_expect(n, d_state, st == QAOA_C128, d_costs, cost_kind(ct), 0.0, ws.partials,
+                       ws.counter, d_out, 0, s, num_sms()));
   return QAOA_OK;
 }
 
@@ -670,9 +893,9 @@ qaoa_status qaoa_overlap(int n, const void *d_state, qaoa_state_type st, const v
   if (r != QAOA_OK) return r;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
-  CK(launch_expect(n, d_state, st == QAOA_C128, d_costs, cost_kind(ct), stats->f_min, ws.partials,
-                   ws.counter, d_out, 1, s, num_sms()),
-     "overlap launch");
+  LAUNCH("expect", ((st == QAOA_C128 ? 16.0 : 8.0) + cost_bytes(ct)) * (double)(1ull << n), s,
+         launch_expect(n, d_state, st == QAOA_C128, d_costs, cost_kind(ct), stats->f_min,
+                       ws.partials, ws.counter, d_out, 1, s, num_sms()));
   return QAOA_OK;
 }
 
@@ -696,6 +919,13 @@ qaoa_status qaoa_grad(int n, const void *d_costs, qaoa_cost_type ct, const qaoa_
                : small_grad<double>(n, d_costs, ct, stats->f_min, gammas, betas, p, d_state, d_lambda, d_out, s);
   }
   CK(cudaMemsetAsync(d_out + 2, 0, sizeof(double) * 2 * (size_t)p, s), "memset grad");
+  CK(cudaMemsetAsync(ws.err, 0, sizeof(unsigned), s), "memset error word");
+  if (st == QAOA_C64 && tma_ok(ct)) {
+    r = tma_forward(n, d_costs, ct, stats, gammas, betas, p, d_state, 1, ws, d_out, s);
+    if (r != QAOA_OK) return r;
+    return tma_backward(n, d_costs, ct, stats, gammas, betas, p, d_state, d_lambda, ws, d_out + 2,
+                        d_out + 2 + p, s);
+  }
   r = st == QAOA_C64
           ? tiled_forward<float>(n, d_costs, ct, stats, gammas, betas, p, d_state, 1, ws, d_out, s)
           : tiled_forward<double>(n, d_costs, ct, stats, gammas, betas, p, d_state, 1, ws, d_out, s);

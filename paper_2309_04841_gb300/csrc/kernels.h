@@ -2,6 +2,7 @@
 // the kernel translation units.  Internal to the library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -47,6 +48,58 @@ cudaError_t launch_fwd(const FwdParams<float> &P, bool high, cudaStream_t s, int
 cudaError_t launch_fwd(const FwdParams<double> &P, bool high, cudaStream_t s, int nsm);
 cudaError_t launch_bwd(const BwdParams<float> &P, bool high, cudaStream_t s, int nsm);
 cudaError_t launch_bwd(const BwdParams<double> &P, bool high, cudaStream_t s, int nsm);
+
+// Launch profiling (profile.cu): returns a record id, or -1 when disabled.
+int prof_begin(cudaStream_t s);
+void prof_end(int id, cudaStream_t s, const char *kind, double bytes);
+
+// ---- complex64 passes streamed by TMA (tma_kernels.cu)
+// Round plans for the TMA 128-byte swizzle (conflict-free at 8 and 16 bytes).
+using PlanTmaF13Low = Plan<13, 5, 256, 0, 3, 0x1F00, 0x001F, 0x00E0,
+                           0x020F, 0x01F0, 0x1C00, 0x01F0, 0x020F, 0x1C00>;
+using PlanTmaF13High = Plan<13, 5, 256, 0, 2, 0x1F00, 0x001F, 0x00E0,
+                            0x01F0, 0x020F, 0x1C00>;
+using PlanTmaB12Low = Plan<12, 4, 256, 0, 3, 0x0F00, 0x001F, 0x00E0,
+                           0x000F, 0x01F0, 0x0E00, 0x00F0, 0x010F, 0x0E00>;
+using PlanTmaB12High = Plan<12, 4, 256, 0, 2, 0x0F00, 0x001F, 0x00E0,
+                            0x00F0, 0x010F, 0x0E00>;
+static_assert(PlanTmaF13Low::valid() && PlanTmaF13High::valid(), "bad TMA F13 plan");
+static_assert(PlanTmaB12Low::valid() && PlanTmaB12High::valid(), "bad TMA B12 plan");
+
+struct alignas(64) TmaFwdParams {
+  CUtensorMap map_psi;   // state, 8-byte elements, 128-byte swizzle
+  CUtensorMap map_cost;  // cost vector, 4-byte elements
+  uint64_t ntiles;
+  int h, cost_kind;
+  Sweep s1, s2;
+  float c1, s1s, c2, s2s;
+  int has_phase, init_plus, reduce;
+  float amp;
+  double fmin_d;
+  double *partials;
+  unsigned *counter;
+  double *out;
+  unsigned *err;
+  PhaseData<float> ph;
+};
+
+struct alignas(64) TmaBwdParams {
+  CUtensorMap map_psi, map_lam, map_cost;
+  uint64_t ntiles;
+  int h, cost_kind;
+  Sweep s1, s2;
+  float c1, s1s, c2, s2s;
+  int has_phase, init_lambda;
+  double *partials;
+  unsigned *counter;
+  double *out_b1, *out_g, *out_b2;
+  unsigned *err;
+  PhaseData<float> ph;
+};
+
+cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, int esz, bool swizzle);
+cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm);
+cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm);
 
 cudaError_t launch_small(const SmallParams<float> &P, cudaStream_t s);
 cudaError_t launch_small(const SmallParams<double> &P, cudaStream_t s);

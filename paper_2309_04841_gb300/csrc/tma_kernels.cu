@@ -1,0 +1,737 @@
+// tma_kernels.cu -- complex64 passes streamed by the Tensor Memory Accelerator.
+//
+// Same math as pass_kernels.cu (Algorithm 1 rotations on a tile window, the
+// phase of Algorithm 3, energy/overlap, and the adjoint inner products), with
+// the data movement done by TMA:
+//   * a persistent CTA per SM: 8 compute warps + 1 producer warp;
+//   * the producer issues cp.async.bulk.tensor loads of the next tiles into
+//     a 2-stage shared-memory ring (mbarrier complete_tx), and bulk tensor
+//     stores of finished tiles back to HBM, so loads, stores and compute of
+//     neighbouring tiles overlap;
+//   * tiles land in shared memory with the TMA 128-byte swizzle; the compute
+//     rounds are laid out so that every shared-memory access of the state is
+//     bank-conflict free under that swizzle.
+// A tile is 2^TB amplitudes: 16 contiguous ones (128 B) times 2^(TB-4) rows at
+// qubits h.. (h = 4 for the contiguous LOW pass).  The tensor map views the
+// state as [16][2^(h-4)][256][2^(TB-12)][rest]; one box is one tile.
+// Every wait on an mbarrier is bounded (about one second of %globaltimer);
+// on timeout the kernel records an error word and returns.
+#include <cuda.h>
+
+#include "qaoa_common.cuh"
+#include "kernels.h"
+
+namespace qaoa {
+
+namespace {
+
+constexpr uint64_t kWaitNs = 1000000000ull;  // bounded waits: 1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the mbarrier phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_try(bar, parity))
+    if (gtimer() - t0 > kWaitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, int c1, int c4,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(0), "r"(0), "r"(c4),
+      "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store(const CUtensorMap *map, const void *src, int c1, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group"
+      " [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(smem_u32(src)), "r"(0), "r"(c1), "r"(0), "r"(0), "r"(c4)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Barrier among the 256 compute threads only (the producer warp never joins).
+__device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// TMA SWIZZLE_128B seen at 8-byte granularity: the 16-byte chunk index inside
+// each 128-byte row is XORed with the row index mod 8.
+__host__ __device__ constexpr uint32_t tswz(uint32_t t) { return t ^ (((t >> 4) & 7u) << 1); }
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return f2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ void rot(float2 &a, float2 &b, float c, float s) {
+  const float2 na = f2(c * a.x + s * b.y, c * a.y - s * b.x);
+  const float2 nb = f2(c * b.x + s * a.y, c * b.y - s * a.x);
+  a = na;
+  b = nb;
+}
+
+template <int EB>
+__device__ __forceinline__ void rot_regs(float2 (&v)[1 << EB], uint32_t m, float c, float s) {
+#pragma unroll
+  for (int i = 0; i < EB; ++i)
+    if ((m >> i) & 1u) {
+#pragma unroll
+      for (int r = 0; r < (1 << EB); ++r)
+        if (!((r >> i) & 1)) rot(v[r], v[r | (1 << i)], c, s);
+    }
+}
+
+template <int EB>
+__device__ __forceinline__ void unrot_acc(float2 (&v)[1 << EB], float2 (&w)[1 << EB], uint32_t m,
+                                          float c, float s, float &acc) {
+#pragma unroll
+  for (int i = 0; i < EB; ++i)
+    if ((m >> i) & 1u) {
+#pragma unroll
+      for (int r = 0; r < (1 << EB); ++r)
+        if (!((r >> i) & 1)) {
+          float2 &pa = v[r], &pb = v[r | (1 << i)], &la = w[r], &lb = w[r | (1 << i)];
+          acc += la.x * pb.y - la.y * pb.x + lb.x * pa.y - lb.y * pa.x;
+          rot(pa, pb, c, s);
+          rot(la, lb, c, s);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pdep_d(uint32_t v, uint32_t mask) {
+  uint32_t out = 0;
+  int k = 0;
+#pragma unroll
+  for (int b = 0; b < 32; ++b)
+    if ((mask >> b) & 1u) {
+      out |= ((v >> k) & 1u) << b;
+      ++k;
+    }
+  return out;
+}
+
+template <class PL, int R>
+__device__ __forceinline__ uint32_t thr_tile() {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  return pdep_d(lane, PL::lane(R)) | pdep_d(warp, PL::warp(R));
+}
+
+// Registers <- shared tile in round-R layout (16-byte accesses when the
+// round holds tile bit 0 in registers).
+template <class PL, int R>
+__device__ __forceinline__ void lds_round(float2 (&v)[PL::NREG], const float2 *buf) {
+  const uint32_t st = tswz(thr_tile<PL, R>());
+  if constexpr ((PL::reg(R) & 1u) != 0u) {
+#pragma unroll
+    for (int r = 0; r < PL::NREG; r += 2) {
+      const float4 q = *reinterpret_cast<const float4 *>(buf + (st ^ tswz(pdep(r, PL::reg(R)))));
+      v[r] = f2(q.x, q.y);
+      v[r + 1] = f2(q.z, q.w);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < PL::NREG; ++r) v[r] = buf[st ^ tswz(pdep(r, PL::reg(R)))];
+  }
+}
+
+template <class PL, int R>
+__device__ __forceinline__ void sts_round(const float2 (&v)[PL::NREG], float2 *buf) {
+  const uint32_t st = tswz(thr_tile<PL, R>());
+  if constexpr ((PL::reg(R) & 1u) != 0u) {
+#pragma unroll
+    for (int r = 0; r < PL::NREG; r += 2)
+      *reinterpret_cast<float4 *>(buf + (st ^ tswz(pdep(r, PL::reg(R))))) =
+          make_float4(v[r].x, v[r].y, v[r + 1].x, v[r + 1].y);
+  } else {
+#pragma unroll
+    for (int r = 0; r < PL::NREG; ++r) buf[st ^ tswz(pdep(r, PL::reg(R)))] = v[r];
+  }
+}
+
+template <class PL, int RF, int RT>
+__device__ __forceinline__ void xp(float2 (&v)[PL::NREG], float2 *buf) {
+  sts_round<PL, RF>(v, buf);
+  cbar();
+  lds_round<PL, RT>(v, buf);
+}
+
+// exp(-i g f) from the raw 32-bit cost word (int32 or float32).
+__device__ __forceinline__ float2 phase_of(const PhaseData<float> &ph, int kind, const float2 *tlo,
+                                           const float2 *thi, uint32_t word) {
+  if (ph.mode == 0) {
+    const uint32_t v = (uint32_t)((int)word - ph.fmin);
+    return cmulf(thi[min(v >> 8, 255u)], tlo[v & 255u]);
+  }
+  float fh, fl;
+  if (kind == kCostI32) {
+    const int f = (int)word;
+    fh = (float)f;
+    fl = (float)((long long)f - (long long)fh);
+  } else {
+    fh = __uint_as_float(word);
+    fl = 0.f;
+  }
+  // g f / 2pi as a float-float: Dekker's two-product p + e = g_hi * fh via fma
+  const float p = ph.g_hi * fh;
+  const float e = fmaf(ph.g_hi, fh, -p);
+  const float r = (p - rintf(p)) + (e + fmaf(ph.g_hi, fl, ph.g_lo * fh));
+  float sn, cs;
+  sincospif(2.0f * r, &sn, &cs);
+  return f2(cs, -sn);
+}
+
+__device__ __forceinline__ float cost_val(int kind, uint32_t word) {
+  return kind == kCostI32 ? (float)(int)word : __uint_as_float(word);
+}
+
+template <class PL, int R>
+__device__ __forceinline__ void phase_round(float2 (&v)[PL::NREG], const uint32_t *cb,
+                                            const PhaseData<float> &ph, int kind,
+                                            const float2 *tlo, const float2 *thi) {
+  const uint32_t tt = thr_tile<PL, R>();
+#pragma unroll
+  for (int r = 0; r < PL::NREG; ++r)
+    v[r] = cmulf(v[r], phase_of(ph, kind, tlo, thi, cb[tt | pdep(r, PL::reg(R))]));
+}
+
+template <class PL, int R>
+__device__ __forceinline__ void eo_round(const float2 (&v)[PL::NREG], const uint32_t *cb, int kind,
+                                         double fmin, float &e, float &o) {
+  const uint32_t tt = thr_tile<PL, R>();
+#pragma unroll
+  for (int r = 0; r < PL::NREG; ++r) {
+    const uint32_t w = cb[tt | pdep(r, PL::reg(R))];
+    const float f = cost_val(kind, w);
+    const float pr = v[r].x * v[r].x + v[r].y * v[r].y;
+    e += pr * f;
+    o += ((double)f == fmin) ? pr : 0.f;
+  }
+}
+
+// Sum of K doubles over the 256 compute threads (fixed order); thread 0 gets it.
+template <int K>
+__device__ __forceinline__ void csum(double (&a)[K], double *red) {
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+  const int w = threadIdx.x >> 5;
+  cbar();
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[w * K + k] = a[k];
+  cbar();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < 8; ++i) s += red[i * K + k];
+      a[k] = s;
+    }
+}
+
+// After the tile loop: the last CTA sums the per-tile partials in tile order.
+template <int K, class Fin>
+__device__ __forceinline__ void final_reduce(const double *partials, uint64_t ntiles,
+                                             unsigned *counter, double *red, Fin fin) {
+  __shared__ int am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1u);
+  __syncthreads();
+  if (!am_last || threadIdx.x >= 256) return;
+  __threadfence();
+  double a[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) a[k] = 0.0;
+  for (uint64_t t = threadIdx.x; t < ntiles; t += 256)
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] += __ldcg(partials + t * K + k);
+  csum<K>(a, red);
+  if (threadIdx.x == 0) {
+    fin(a);
+    *counter = 0u;
+  }
+}
+
+// Shared-memory layout (offsets from a 1024-byte aligned base): two stage
+// buffers of the state (and lambda), two of the cost vector, the phase
+// tables, the mbarriers and the reduction scratch.
+struct Lay {
+  uint32_t tile_bytes, lam_off, cost_off, cost_bytes, tab_off, bar_off, red_off;
+};
+
+__device__ __forceinline__ Lay layout(uint32_t tile_elems, bool two, bool cost) {
+  Lay L;
+  L.tile_bytes = tile_elems * 8u;
+  L.lam_off = 2u * L.tile_bytes;
+  L.cost_off = L.lam_off + (two ? 2u * L.tile_bytes : 0u);
+  L.cost_bytes = cost ? tile_elems * 4u : 0u;
+  L.tab_off = L.cost_off + 2u * L.cost_bytes;
+  L.bar_off = L.tab_off + 512u * 8u;
+  L.red_off = L.bar_off + 32u;
+  return L;
+}
+
+__device__ __forceinline__ unsigned char *aligned_base(unsigned char *raw) {
+  const uint32_t a = smem_u32(raw);
+  return raw + ((1024u - (a & 1023u)) & 1023u);
+}
+
+}  // namespace
+
+size_t tma_smem_bytes(int tb, bool two, bool cost) {
+  const size_t te = (size_t)1 << tb;
+  return 1024 + 2 * te * 8 * (two ? 2 : 1) + (cost ? 2 * te * 4 : 0) + 512 * 8 + 32 + 8 * 3 * 8;
+}
+
+// ------------------------------------------------------------- forward
+
+template <class PL>
+__global__ void __launch_bounds__(288, 1) k_fwd_tma(const __grid_constant__ TmaFwdParams P) {
+  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB;
+  extern __shared__ unsigned char smem_raw[];
+  const bool need_cost = P.has_phase || P.reduce;
+  unsigned char *base = aligned_base(smem_raw);
+  const Lay L = layout(1u << PL::TB, false, need_cost);
+  float2 *tlo = reinterpret_cast<float2 *>(base + L.tab_off), *thi = tlo + 256;
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off), *empty = full + 2;
+  double *red = reinterpret_cast<double *>(base + L.red_off);
+  const int tid = threadIdx.x;
+  const uint32_t psi_bytes = L.tile_bytes, cost_bytes = L.cost_bytes;
+  const int midbits = P.h - 4;
+
+  if (P.has_phase && P.ph.mode == 0)
+    for (int i = tid; i < 256; i += 288) {
+      tlo[i] = P.ph.tab_lo[i];
+      thi[i] = P.ph.tab_hi[i];
+    }
+  __shared__ int s_abort;
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 256);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (tid >= 256) {
+    // ---------------- producer warp: TMA loads and stores
+    if (tid == 256) {
+      auto issue = [&](uint64_t T, int s) {
+        const int c1 = (int)(T & ((1ull << midbits) - 1ull)), c4 = (int)(T >> midbits);
+        mbar_expect_tx(&full[s], (P.init_plus ? 0u : psi_bytes) + (need_cost ? cost_bytes : 0u));
+        if (!P.init_plus) tma_load(reinterpret_cast<float2 *>(base + s * L.tile_bytes), &P.map_psi, c1, c4, &full[s]);
+        if (need_cost) tma_load(reinterpret_cast<uint32_t *>(base + L.cost_off + s * L.cost_bytes), &P.map_cost, c1, c4, &full[s]);
+      };
+      for (int i = 0; i < 2; ++i) {
+        const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
+        if (T < P.ntiles) issue(T, i);
+      }
+      for (int i = 0;; ++i) {
+        const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
+        if (T >= P.ntiles) break;
+        const int s = i & 1;
+        if (!mbar_wait(&empty[s], (i >> 1) & 1)) {
+          atomicExch(P.err, 1u);
+          break;
+        }
+        tma_store(&P.map_psi, reinterpret_cast<float2 *>(base + s * L.tile_bytes), (int)(T & ((1ull << midbits) - 1ull)), (int)(T >> midbits));
+        bulk_commit();
+        const uint64_t T2 = T + 2ull * gridDim.x;
+        if (T2 < P.ntiles) {
+          bulk_wait_read0();
+          issue(T2, s);
+        }
+      }
+      bulk_wait0();
+    }
+  } else {
+    // ---------------- compute warps
+    const bool has1 = (P.s1.m[0] | P.s1.m[1] | P.s1.m[2]) != 0;
+    const bool has2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2]) != 0;
+    for (int i = 0;; ++i) {
+      const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
+      if (T >= P.ntiles) break;
+      const int s = i & 1;
+      // every compute thread takes the same decision after a timeout, so no
+      // thread is left waiting at a barrier the others skipped
+      if (!mbar_wait(&full[s], (i >> 1) & 1)) {
+        s_abort = 1;
+        atomicExch(P.err, 1u);
+      }
+      cbar();
+      if (s_abort) break;
+      float2 *buf = reinterpret_cast<float2 *>(base + s * L.tile_bytes);
+      const uint32_t *cb = reinterpret_cast<uint32_t *>(base + L.cost_off + s * L.cost_bytes);
+      float2 v[NREG];
+      if (P.init_plus) {
+#pragma unroll
+        for (int r = 0; r < NREG; ++r) v[r] = f2(P.amp, 0.f);
+      } else {
+        lds_round<PL, 0>(v, buf);
+      }
+      bool final0;
+      if (has1) {
+        rot_regs<EB>(v, P.s1.m[0], P.c1, P.s1s);
+        xp<PL, 0, 1>(v, buf);
+        rot_regs<EB>(v, P.s1.m[1], P.c1, P.s1s);
+        if constexpr (NR == 3) {
+          xp<PL, 1, 2>(v, buf);
+          rot_regs<EB>(v, P.s1.m[2], P.c1, P.s1s);
+        }
+        if (P.has_phase) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tlo, thi);
+        if (has2) {
+          rot_regs<EB>(v, P.s2.m[NR - 1], P.c2, P.s2s);
+          if constexpr (NR == 3) {
+            xp<PL, 2, 1>(v, buf);
+            rot_regs<EB>(v, P.s2.m[1], P.c2, P.s2s);
+          }
+          xp<PL, 1, 0>(v, buf);
+          rot_regs<EB>(v, P.s2.m[0], P.c2, P.s2s);
+          final0 = true;
+        } else {
+          final0 = false;
+        }
+      } else {
+        if (P.has_phase) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tlo, thi);
+        rot_regs<EB>(v, P.s2.m[0], P.c2, P.s2s);
+        xp<PL, 0, 1>(v, buf);
+        rot_regs<EB>(v, P.s2.m[1], P.c2, P.s2s);
+        if constexpr (NR == 3) {
+          xp<PL, 1, 2>(v, buf);
+          rot_regs<EB>(v, P.s2.m[2], P.c2, P.s2s);
+        }
+        final0 = false;
+      }
+      float e = 0.f, o = 0.f;
+      if (final0) {
+        if (P.reduce) eo_round<PL, 0>(v, cb, P.cost_kind, P.fmin_d, e, o);
+        sts_round<PL, 0>(v, buf);
+      } else {
+        if (P.reduce) eo_round<PL, NR - 1>(v, cb, P.cost_kind, P.fmin_d, e, o);
+        sts_round<PL, NR - 1>(v, buf);
+      }
+      fence_async_smem();
+      mbar_arrive(&empty[s]);
+      if (P.reduce) {
+        double a[2] = {(double)e, (double)o};
+        csum<2>(a, red);
+        if (tid == 0) {
+          P.partials[T * 2] = a[0];
+          P.partials[T * 2 + 1] = a[1];
+        }
+      }
+    }
+  }
+  if (P.reduce) {
+    double *out = P.out;
+    final_reduce<2>(P.partials, P.ntiles, P.counter, red, [out](double(&a)[2]) {
+      out[0] = a[0];
+      out[1] = a[1];
+    });
+  }
+}
+
+// ------------------------------------------------------------- adjoint
+
+template <class PL>
+__global__ void __launch_bounds__(288, 1) k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
+  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB;
+  extern __shared__ unsigned char smem_raw[];
+  const bool need_cost = P.has_phase || P.init_lambda;
+  unsigned char *base = aligned_base(smem_raw);
+  const Lay L = layout(1u << PL::TB, true, need_cost);
+  float2 *tlo = reinterpret_cast<float2 *>(base + L.tab_off), *thi = tlo + 256;
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off), *empty = full + 2;
+  double *red = reinterpret_cast<double *>(base + L.red_off);
+  const int tid = threadIdx.x;
+  const uint32_t vec_bytes = L.tile_bytes, cost_bytes = L.cost_bytes;
+  const int midbits = P.h - 4;
+
+  if (P.has_phase && P.ph.mode == 0)
+    for (int i = tid; i < 256; i += 288) {
+      tlo[i] = P.ph.tab_lo[i];
+      thi[i] = P.ph.tab_hi[i];
+    }
+  __shared__ int s_abort;
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 256);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (tid >= 256) {
+    if (tid == 256) {
+      auto issue = [&](uint64_t T, int s) {
+        const int c1 = (int)(T & ((1ull << midbits) - 1ull)), c4 = (int)(T >> midbits);
+        mbar_expect_tx(&full[s], vec_bytes + (P.init_lambda ? 0u : vec_bytes) +
+                                       (need_cost ? cost_bytes : 0u));
+        tma_load(reinterpret_cast<float2 *>(base + s * L.tile_bytes), &P.map_psi, c1, c4, &full[s]);
+        if (!P.init_lambda) tma_load(reinterpret_cast<float2 *>(base + L.lam_off + s * L.tile_bytes), &P.map_lam, c1, c4, &full[s]);
+        if (need_cost) tma_load(reinterpret_cast<uint32_t *>(base + L.cost_off + s * L.cost_bytes), &P.map_cost, c1, c4, &full[s]);
+      };
+      for (int i = 0; i < 2; ++i) {
+        const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
+        if (T < P.ntiles) issue(T, i);
+      }
+      for (int i = 0;; ++i) {
+        const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
+        if (T >= P.ntiles) break;
+        const int s = i & 1;
+        if (!mbar_wait(&empty[s], (i >> 1) & 1)) {
+          atomicExch(P.err, 1u);
+          break;
+        }
+        const int c1 = (int)(T & ((1ull << midbits) - 1ull)), c4 = (int)(T >> midbits);
+        tma_store(&P.map_psi, reinterpret_cast<float2 *>(base + s * L.tile_bytes), c1, c4);
+        tma_store(&P.map_lam, reinterpret_cast<float2 *>(base + L.lam_off + s * L.tile_bytes), c1, c4);
+        bulk_commit();
+        const uint64_t T2 = T + 2ull * gridDim.x;
+        if (T2 < P.ntiles) {
+          bulk_wait_read0();
+          issue(T2, s);
+        }
+      }
+      bulk_wait0();
+    }
+  } else {
+    const bool has2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2]) != 0;
+    for (int i = 0;; ++i) {
+      const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
+      if (T >= P.ntiles) break;
+      const int s = i & 1;
+      // every compute thread takes the same decision after a timeout, so no
+      // thread is left waiting at a barrier the others skipped
+      if (!mbar_wait(&full[s], (i >> 1) & 1)) {
+        s_abort = 1;
+        atomicExch(P.err, 1u);
+      }
+      cbar();
+      if (s_abort) break;
+      float2 *bv = reinterpret_cast<float2 *>(base + s * L.tile_bytes), *bw = reinterpret_cast<float2 *>(base + L.lam_off + s * L.tile_bytes);
+      const uint32_t *cb = reinterpret_cast<uint32_t *>(base + L.cost_off + s * L.cost_bytes);
+      float2 v[NREG], w[NREG];
+      lds_round<PL, 0>(v, bv);
+      if (P.init_lambda) {
+        // lambda = f psi: the derivative of E = <psi|f|psi> with respect to psi^*
+        const uint32_t tt = thr_tile<PL, 0>();
+#pragma unroll
+        for (int r = 0; r < NREG; ++r) {
+          const float f = cost_val(P.cost_kind, cb[tt | pdep(r, PL::reg(0))]);
+          w[r] = f2(f * v[r].x, f * v[r].y);
+        }
+      } else {
+        lds_round<PL, 0>(w, bw);
+      }
+      float a1 = 0.f, ag = 0.f, a2 = 0.f;
+      unrot_acc<EB>(v, w, P.s1.m[0], P.c1, P.s1s, a1);
+      sts_round<PL, 0>(v, bv);
+      sts_round<PL, 0>(w, bw);
+      cbar();
+      lds_round<PL, 1>(v, bv);
+      lds_round<PL, 1>(w, bw);
+      unrot_acc<EB>(v, w, P.s1.m[1], P.c1, P.s1s, a1);
+      if constexpr (NR == 3) {
+        sts_round<PL, 1>(v, bv);
+        sts_round<PL, 1>(w, bw);
+        cbar();
+        lds_round<PL, 2>(v, bv);
+        lds_round<PL, 2>(w, bw);
+        unrot_acc<EB>(v, w, P.s1.m[2], P.c1, P.s1s, a1);
+      }
+      if (P.has_phase) {
+        // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
+        const uint32_t tt = thr_tile<PL, NR - 1>();
+#pragma unroll
+        for (int r = 0; r < NREG; ++r) {
+          const uint32_t word = cb[tt | pdep(r, PL::reg(NR - 1))];
+          const float f = cost_val(P.cost_kind, word);
+          ag += f * (w[r].x * v[r].y - w[r].y * v[r].x);
+          const float2 ph = phase_of(P.ph, P.cost_kind, tlo, thi, word);
+          v[r] = cmulf(v[r], ph);
+          w[r] = cmulf(w[r], ph);
+        }
+      }
+      bool final0 = false;
+      if (has2) {
+        unrot_acc<EB>(v, w, P.s2.m[NR - 1], P.c2, P.s2s, a2);
+        if constexpr (NR == 3) {
+          sts_round<PL, 2>(v, bv);
+          sts_round<PL, 2>(w, bw);
+          cbar();
+          lds_round<PL, 1>(v, bv);
+          lds_round<PL, 1>(w, bw);
+          unrot_acc<EB>(v, w, P.s2.m[1], P.c2, P.s2s, a2);
+        }
+        sts_round<PL, 1>(v, bv);
+        sts_round<PL, 1>(w, bw);
+        cbar();
+        lds_round<PL, 0>(v, bv);
+        lds_round<PL, 0>(w, bw);
+        unrot_acc<EB>(v, w, P.s2.m[0], P.c2, P.s2s, a2);
+        final0 = true;
+      }
+      if (final0) {
+        sts_round<PL, 0>(v, bv);
+        sts_round<PL, 0>(w, bw);
+      } else {
+        sts_round<PL, NR - 1>(v, bv);
+        sts_round<PL, NR - 1>(w, bw);
+      }
+      fence_async_smem();
+      mbar_arrive(&empty[s]);
+      double a[3] = {(double)a1, (double)ag, (double)a2};
+      csum<3>(a, red);
+      if (tid == 0) {
+        P.partials[T * 3] = a[0];
+        P.partials[T * 3 + 1] = a[1];
+        P.partials[T * 3 + 2] = a[2];
+      }
+    }
+  }
+  double *o1 = P.out_b1, *og = P.out_g, *o2 = P.out_b2;
+  final_reduce<3>(P.partials, P.ntiles, P.counter, red, [=](double(&a)[3]) {
+    if (o1) *o1 += 2.0 * a[0];
+    if (og) *og += 2.0 * a[1];
+    if (o2) *o2 += 2.0 * a[2];
+  });
+}
+
+// ---------------------------------------------------------------- host side
+
+namespace {
+
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                              const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                              const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+// 5-D tile view of a 2^n vector of `esz`-byte elements for tiles of 2^tb
+// elements: [16][2^(h-4)][256][2^(tb-12)][2^(n-h-(tb-4))]; one box = one tile.
+cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, int esz, bool swizzle) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const int hi = tb - 12;  // extra high-segment bits beyond 256 rows
+  cuuint64_t dims[5] = {16, 1ull << (h - 4), 256, 1ull << hi, 1ull << (n - h - (tb - 4))};
+  const cuuint64_t e = (cuuint64_t)esz;
+  cuuint64_t strides[4] = {16 * e, (1ull << h) * e, (1ull << (h + 8)) * e, (1ull << (h + 8 + hi)) * e};
+  cuuint32_t box[5] = {16, 1, 256, (cuuint32_t)(1u << hi), 1};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  const CUtensorMapDataType dt = esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+  const CUresult r = fn(map, dt, 5, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <class PL>
+static cudaError_t launch_fwd_tma_t(const TmaFwdParams &P, cudaStream_t s, int nsm) {
+  const size_t smem = tma_smem_bytes(PL::TB, false, P.has_phase || P.reduce);
+  static bool init = false;
+  if (!init) {
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_tma<PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tma_smem_bytes(PL::TB, false, true));
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  const uint64_t grid = P.ntiles < (uint64_t)nsm ? P.ntiles : (uint64_t)nsm;
+  k_fwd_tma<PL><<<(unsigned)grid, 288, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
+template <class PL>
+static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int nsm) {
+  const size_t smem = tma_smem_bytes(PL::TB, true, P.has_phase || P.init_lambda);
+  static bool init = false;
+  if (!init) {
+    cudaError_t e = cudaFuncSetAttribute(k_bwd_tma<PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tma_smem_bytes(PL::TB, true, true));
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  const uint64_t grid = P.ntiles < (uint64_t)nsm ? P.ntiles : (uint64_t)nsm;
+  k_bwd_tma<PL><<<(unsigned)grid, 288, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm) {
+  return high ? launch_fwd_tma_t<PlanTmaF13High>(P, s, nsm) : launch_fwd_tma_t<PlanTmaF13Low>(P, s, nsm);
+}
+
+cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {
+  return high ? launch_bwd_tma_t<PlanTmaB12High>(P, s, nsm) : launch_bwd_tma_t<PlanTmaB12Low>(P, s, nsm);
+}
+
+}  // namespace qaoa

@@ -29,6 +29,11 @@ class QAOAError(RuntimeError):
         self.status = status
 
 
+class ProfEntry(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_uint64), ("ms", C.c_double),
+                ("bytes", C.c_double)]
+
+
 class CostStats(C.Structure):
     _fields_ = [("f_min", C.c_double), ("f_max", C.c_double), ("n_min", C.c_uint64)]
 
@@ -63,6 +68,9 @@ def lib():
             "qaoa_expectation": ([I, P, I, P, I, P, Z, P, P], I),
             "qaoa_overlap": ([I, P, I, P, I, P, P, Z, P, P], I),
             "qaoa_grad": ([I, P, I, P, P, P, I, P, P, I, P, Z, P, P], I),
+            "qaoa_workspace_check": ([P, Z, P], I),
+            "qaoa_profile_enable": ([I], I),
+            "qaoa_profile_read": ([P, I, P, I], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -164,6 +172,12 @@ def workspace_bytes(n):
 def workspace(n, device="cuda"):
     torch = _torch()
     return torch.empty(workspace_bytes(n), dtype=torch.uint8, device=device)
+
+
+def workspace_check(work):
+    """Raises QAOAError(timeout) if a kernel that used `work` gave up on a
+    bounded device-side wait; synchronises the current stream."""
+    _check(lib().qaoa_workspace_check(_ptr(work), work.numel(), _stream()))
 
 
 def precompute_costs(n, terms, cost_type=COST_I32, out=None):
@@ -313,3 +327,18 @@ def qaoa_energy(costs, stats, gammas, betas, state_type=C64):
 
         _EnergyFn.fn = QAOAEnergy
     return _EnergyFn.fn.apply(gammas, betas, costs, stats, state_type)
+
+
+# -------------------------------------------------------------- profiling
+
+def profile_enable(on=True):
+    _check(lib().qaoa_profile_enable(1 if on else 0))
+
+
+def profile_read(reset=True):
+    """{kind: {"launches", "ms", "bytes"}} for the library's recorded launches."""
+    buf = (ProfEntry * 64)()
+    cnt = C.c_int(0)
+    _check(lib().qaoa_profile_read(buf, 64, C.byref(cnt), 1 if reset else 0))
+    return {buf[i].name.decode(): {"launches": int(buf[i].launches), "ms": float(buf[i].ms),
+                                   "bytes": float(buf[i].bytes)} for i in range(min(cnt.value, 64))}

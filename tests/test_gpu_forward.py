@@ -199,3 +199,26 @@ def test_labs30_energy_vs_stored_oracle(Q, name):
     assert abs(nrm - 1) < 1e-5
     del state
     T.cuda.empty_cache()
+
+
+def test_workspace_check_clean_after_runs(Q):
+    n = 20
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    work = Q.workspace(n)
+    Q.simulate(fd, stats, [0.1, 0.2], [0.3, 0.4], work=work)
+    Q.workspace_check(work)
+    Q.grad(fd, stats, [0.1, 0.2], [0.3, 0.4], work=work)
+    Q.workspace_check(work)
+
+
+@pytest.mark.parametrize("n", [13, 21, 22, 26])
+def test_f64_costs_and_c64_state(Q, n):
+    # float64 costs with a complex64 state take the non-TMA pass kernels
+    terms = I.random_terms(n, 20, 3, max_order=2, integer=False)
+    f = oracle.costs_terms_real(n, terms)
+    fd = Q.precompute_costs(n, terms, Q.COST_F64)
+    g = I.angles(2, 5, 0, 0.5)
+    b = I.angles(2, 6)
+    got, ref, o, E, O = run_case(Q, n, f, fd, g, b, "c64")
+    assert rel_state_err(got, ref) < TOL["c64"]["state"]
