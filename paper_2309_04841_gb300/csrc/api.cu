@@ -10,6 +10,7 @@
 // Nothing here allocates device memory: scratch lives in the caller's
 // workspace, per-layer constants travel in the kernel parameter blocks.
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -111,9 +112,11 @@ qaoa_status check_angles(const double *g, const double *b, int p) {
 
 const double kTwoPi = 6.283185307179586476925286766559;
 
-// Phase data for multiplying by exp(-i g f).
+// Phase data for multiplying by exp(-i g f) (times `scale` in table mode;
+// the computed mode leaves the scale to the kernel).
 template <typename Real>
-void make_phase(PhaseData<Real> &ph, double g, qaoa_cost_type ct, const qaoa_cost_stats *stats) {
+void make_phase(PhaseData<Real> &ph, double g, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                std::complex<double> scale = 1.0) {
   using C2 = typename C2T<Real>::type;
   memset(&ph, 0, sizeof(ph));
   const double range = stats ? stats->f_max - stats->f_min : 1e300;
@@ -125,7 +128,8 @@ void make_phase(PhaseData<Real> &ph, double g, qaoa_cost_type ct, const qaoa_cos
       const double a = g * (double)j;
       ph.tab_lo[j] = C2{(Real)cos(a), (Real)-sin(a)};
       const double b = g * ((double)stats->f_min + 256.0 * (double)j);
-      ph.tab_hi[j] = C2{(Real)cos(b), (Real)-sin(b)};
+      const std::complex<double> hv = std::complex<double>(cos(b), -sin(b)) * scale;
+      ph.tab_hi[j] = C2{(Real)hv.real(), (Real)hv.imag()};
     }
   } else {
     ph.mode = 1;
@@ -465,6 +469,33 @@ qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qao
 
 bool tma_ok(qaoa_cost_type ct) { return ct == QAOA_COST_I32 || ct == QAOA_COST_F32; }
 
+// Reduced ("tan") form of exp(-i b X) (forward) or exp(+i b X) (adjoint):
+// exp(-/+ i b X) = sigma * G with |tau| <= 1 (see TmaFwdParams).
+struct TanRot {
+  float tau;
+  int form;
+  std::complex<double> sigma;
+};
+
+TanRot tan_rot(double beta, bool adjoint) {
+  const double c = cos(beta), s = sin(beta);
+  TanRot r;
+  if (fabs(c) >= fabs(s)) {
+    r.form = 0;
+    r.tau = (float)(adjoint ? -s / c : s / c);
+    r.sigma = c;
+  } else {
+    r.form = 1;
+    r.tau = (float)(adjoint ? -c / s : c / s);
+    r.sigma = std::complex<double>(0.0, adjoint ? s : -s);
+  }
+  return r;
+}
+
+int popc8(uint8_t m) { return __builtin_popcount((unsigned)m); }
+
+float2 f2c(std::complex<double> z) { return make_float2((float)z.real(), (float)z.imag()); }
+
 qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
                         const double *gam, const double *bet, int p, void *state, int init_plus,
                         const Ws &ws, double *d_out, cudaStream_t s) {
@@ -478,6 +509,7 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
   static TmaFwdParams P;  // parameter block; launches copy it, calls are serialised
   static std::mutex *mu = new std::mutex();
   std::lock_guard<std::mutex> lock(*mu);
+  std::complex<double> sig = 1.0;  // scale the stored state still owes
   for (const PassOp &op : ops) {
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
@@ -488,18 +520,33 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
     P.h = h;
     P.cost_kind = cost_kind(ct);
     const bool two = op.l1 >= 0 && op.l2 >= 0;
+    const int nrot = __builtin_popcount(G.rot);
     if (op.l1 >= 0) {
       P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
-      P.c1 = (float)cos(bet[op.l1]);
-      P.s1s = (float)sin(bet[op.l1]);
+      const TanRot R = tan_rot(bet[op.l1], false);
+      P.tau1 = R.tau;
+      P.form1 = R.form;
+      sig *= std::pow(R.sigma, nrot);
+    }
+    P.has_phase = op.lp >= 0;
+    if (P.has_phase) {
+      // the pending scale rides on the phase multiply
+      make_phase<float>(P.ph, gam[op.lp], ct, stats, sig);
+      P.scl_phase = f2c(sig);
+      sig = 1.0;
     }
     if (op.l2 >= 0) {
       P.s2 = G.high ? make_sweep<High>(G.rot, !two) : make_sweep<Low>(G.rot, !two);
-      P.c2 = (float)cos(bet[op.l2]);
-      P.s2s = (float)sin(bet[op.l2]);
+      const TanRot R = tan_rot(bet[op.l2], false);
+      P.tau2 = R.tau;
+      P.form2 = R.form;
+      sig *= std::pow(R.sigma, nrot);
     }
-    P.has_phase = op.lp >= 0;
-    if (P.has_phase) make_phase<float>(P.ph, gam[op.lp], ct, stats);
+    if (&op == &ops.back()) {
+      P.end_scale = 1;
+      P.scl_end = f2c(sig);
+      sig = 1.0;
+    }
     P.init_plus = op.init;
     P.amp = (float)(1.0 / sqrt(ldexp(1.0, n)));
     P.reduce = op.reduce;
@@ -531,6 +578,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
   static TmaBwdParams P;
   static std::mutex *mu = new std::mutex();
   std::lock_guard<std::mutex> lock(*mu);
+  std::complex<double> sig = 1.0;  // common scale psi and lambda carry
   for (const PassOp &op : ops) {
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
@@ -542,18 +590,37 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     P.h = h;
     P.cost_kind = cost_kind(ct);
     P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
-    P.c1 = (float)cos(bet[op.l1]);
-    P.s1s = (float)-sin(bet[op.l1]);
+    {
+      const TanRot R = tan_rot(bet[op.l1], true);
+      P.tau1 = R.tau;
+      P.form1 = R.form;
+      // stored vectors are the true ones divided by sig, so a raw inner
+      // product is the true one divided by |sig|^2
+      for (int r = 0; r < Low::NR; ++r) {  // the kernel walks s1 upward
+        P.w1[r] = (float)std::norm(sig);
+        sig *= std::pow(R.sigma, popc8(P.s1.m[r]));
+      }
+    }
     P.out_b1 = d_grad_b + op.l1;
     if (op.lp >= 0) {
       P.has_phase = 1;
-      make_phase<float>(P.ph, -gam[op.lp], ct, stats);
+      P.wg = (float)std::norm(sig);
+      // the un-phase multiply also pays the pending scale
+      make_phase<float>(P.ph, -gam[op.lp], ct, stats, sig);
+      P.scl_phase = f2c(sig);
+      sig = 1.0;
       P.out_g = d_grad_g + op.lp;
     }
     if (op.l2 >= 0) {
       P.s2 = G.high ? make_sweep<High>(G.rot, false) : make_sweep<Low>(G.rot, false);
-      P.c2 = (float)cos(bet[op.l2]);
-      P.s2s = (float)-sin(bet[op.l2]);
+      const TanRot R = tan_rot(bet[op.l2], true);
+      P.tau2 = R.tau;
+      P.form2 = R.form;
+      for (int k = 0; k < Low::NR; ++k) {  // and s2 downward
+        const int r = Low::NR - 1 - k;
+        P.w2[r] = (float)std::norm(sig);
+        sig *= std::pow(R.sigma, popc8(P.s2.m[r]));
+      }
       P.out_b2 = d_grad_b + op.l2;
     }
     P.init_lambda = op.init;

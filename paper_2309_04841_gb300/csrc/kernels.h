@@ -66,13 +66,22 @@ using PlanTmaB12High = Plan<12, 4, 256, 0, 2, 0x0F00, 0x001F, 0x00E0,
 static_assert(PlanTmaF13Low::valid() && PlanTmaF13High::valid(), "bad TMA F13 plan");
 static_assert(PlanTmaB12Low::valid() && PlanTmaB12High::valid(), "bad TMA B12 plan");
 
+// Rotations run in reduced ("tan") form: each exp(-i b X) = sigma * G with
+//   form 0: sigma = cos b,     G(a, b) = (a - i t b, b - i t a),  t = tan b
+//   form 1: sigma = -i sin b,  G(a, b) = (b + i u a, a + i u b),  u = cot b
+// (the adjoint uses -b), |t|, |u| <= 1; the host tracks the product of the
+// sigmas and folds it into the next phase multiply (scl_phase, or the phase
+// table) or applies it at the end of the pass (scl_end).
 struct alignas(64) TmaFwdParams {
   CUtensorMap map_psi;   // state, 8-byte elements, 128-byte swizzle
   CUtensorMap map_cost;  // cost vector, 4-byte elements
   uint64_t ntiles;
   int h, cost_kind;
   Sweep s1, s2;
-  float c1, s1s, c2, s2s;
+  float tau1, tau2;
+  int form1, form2;
+  float2 scl_phase, scl_end;
+  int end_scale;
   int has_phase, init_plus, reduce;
   float amp;
   double fmin_d;
@@ -88,7 +97,11 @@ struct alignas(64) TmaBwdParams {
   uint64_t ntiles;
   int h, cost_kind;
   Sweep s1, s2;
-  float c1, s1s, c2, s2s;
+  float tau1, tau2;
+  int form1, form2;
+  float2 scl_phase;   // multiplies the un-phase factor (computed mode)
+  float w1[4], w2[4]; // |scale|^2 weights of the inner products taken in each round
+  float wg;           // |scale|^2 weight of the d/d gamma inner product
   int has_phase, init_lambda;
   double *partials;
   unsigned *counter;

@@ -112,39 +112,57 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return f2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__device__ __forceinline__ void rot(float2 &a, float2 &b, float c, float s) {
-  const float2 na = f2(c * a.x + s * b.y, c * a.y - s * b.x);
-  const float2 nb = f2(c * b.x + s * a.y, c * b.y - s * a.x);
-  a = na;
-  b = nb;
+// Reduced-form rotation of the masked register bits (see TmaFwdParams).
+template <int EB>
+__device__ __forceinline__ void rot_tan(float2 (&v)[1 << EB], uint32_t m, float tau, int form) {
+  if (form == 0) {
+#pragma unroll
+    for (int i = 0; i < EB; ++i)
+      if ((m >> i) & 1u) {
+#pragma unroll
+        for (int r = 0; r < (1 << EB); ++r)
+          if (!((r >> i) & 1)) {
+            const float2 a = v[r], b = v[r | (1 << i)];
+            v[r] = f2(fmaf(tau, b.y, a.x), fmaf(-tau, b.x, a.y));
+            v[r | (1 << i)] = f2(fmaf(tau, a.y, b.x), fmaf(-tau, a.x, b.y));
+          }
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < EB; ++i)
+      if ((m >> i) & 1u) {
+#pragma unroll
+        for (int r = 0; r < (1 << EB); ++r)
+          if (!((r >> i) & 1)) {
+            const float2 a = v[r], b = v[r | (1 << i)];
+            v[r] = f2(fmaf(-tau, a.y, b.x), fmaf(tau, a.x, b.y));
+            v[r | (1 << i)] = f2(fmaf(-tau, b.y, a.x), fmaf(tau, b.x, a.y));
+          }
+      }
+  }
 }
 
+// Adjoint: reduced-form un-rotation of psi (v) and lambda (w), adding the raw
+// Im <lambda| X_q |psi> of each pair first; the round's sum is weighted by wr
+// (the squared scale the stored vectors owe at this point).
 template <int EB>
-__device__ __forceinline__ void rot_regs(float2 (&v)[1 << EB], uint32_t m, float c, float s) {
-#pragma unroll
-  for (int i = 0; i < EB; ++i)
-    if ((m >> i) & 1u) {
-#pragma unroll
-      for (int r = 0; r < (1 << EB); ++r)
-        if (!((r >> i) & 1)) rot(v[r], v[r | (1 << i)], c, s);
-    }
-}
-
-template <int EB>
-__device__ __forceinline__ void unrot_acc(float2 (&v)[1 << EB], float2 (&w)[1 << EB], uint32_t m,
-                                          float c, float s, float &acc) {
+__device__ __forceinline__ void unrot_tan(float2 (&v)[1 << EB], float2 (&w)[1 << EB], uint32_t m,
+                                          float tau, int form, float wr, float &acc) {
+  if (m == 0u) return;
+  float racc = 0.f;
 #pragma unroll
   for (int i = 0; i < EB; ++i)
     if ((m >> i) & 1u) {
 #pragma unroll
       for (int r = 0; r < (1 << EB); ++r)
         if (!((r >> i) & 1)) {
-          float2 &pa = v[r], &pb = v[r | (1 << i)], &la = w[r], &lb = w[r | (1 << i)];
-          acc += la.x * pb.y - la.y * pb.x + lb.x * pa.y - lb.y * pa.x;
-          rot(pa, pb, c, s);
-          rot(la, lb, c, s);
+          const float2 pa = v[r], pb = v[r | (1 << i)], la = w[r], lb = w[r | (1 << i)];
+          racc += la.x * pb.y - la.y * pb.x + lb.x * pa.y - lb.y * pa.x;
         }
     }
+  acc = fmaf(racc, wr, acc);
+  rot_tan<EB>(v, m, tau, form);
+  rot_tan<EB>(w, m, tau, form);
 }
 
 __device__ __forceinline__ uint32_t pdep_d(uint32_t v, uint32_t mask) {
@@ -233,14 +251,21 @@ __device__ __forceinline__ float cost_val(int kind, uint32_t word) {
   return kind == kCostI32 ? (float)(int)word : __uint_as_float(word);
 }
 
+// v <- v * exp(-i g f) (* scl in computed mode; table mode has it folded in).
 template <class PL, int R>
 __device__ __forceinline__ void phase_round(float2 (&v)[PL::NREG], const uint32_t *cb,
                                             const PhaseData<float> &ph, int kind,
-                                            const float2 *tlo, const float2 *thi) {
+                                            const float2 *tlo, const float2 *thi, float2 scl) {
   const uint32_t tt = thr_tile<PL, R>();
+  if (ph.mode == 0) {
 #pragma unroll
-  for (int r = 0; r < PL::NREG; ++r)
-    v[r] = cmulf(v[r], phase_of(ph, kind, tlo, thi, cb[tt | pdep(r, PL::reg(R))]));
+    for (int r = 0; r < PL::NREG; ++r)
+      v[r] = cmulf(v[r], phase_of(ph, kind, tlo, thi, cb[tt | pdep(r, PL::reg(R))]));
+  } else {
+#pragma unroll
+    for (int r = 0; r < PL::NREG; ++r)
+      v[r] = cmulf(v[r], cmulf(scl, phase_of(ph, kind, tlo, thi, cb[tt | pdep(r, PL::reg(R))])));
+  }
 }
 
 template <class PL, int R>
@@ -310,13 +335,13 @@ struct Lay {
   uint32_t tile_bytes, lam_off, cost_off, cost_bytes, tab_off, bar_off, red_off;
 };
 
-__device__ __forceinline__ Lay layout(uint32_t tile_elems, bool two, bool cost) {
+__device__ __forceinline__ Lay layout(uint32_t tile_elems, bool two, bool cost, uint32_t ns) {
   Lay L;
   L.tile_bytes = tile_elems * 8u;
-  L.lam_off = 2u * L.tile_bytes;
-  L.cost_off = L.lam_off + (two ? 2u * L.tile_bytes : 0u);
+  L.lam_off = ns * L.tile_bytes;
+  L.cost_off = L.lam_off + (two ? ns * L.tile_bytes : 0u);
   L.cost_bytes = cost ? tile_elems * 4u : 0u;
-  L.tab_off = L.cost_off + 2u * L.cost_bytes;
+  L.tab_off = L.cost_off + ns * L.cost_bytes;
   L.bar_off = L.tab_off + 512u * 8u;
   L.red_off = L.bar_off + 32u;
   return L;
@@ -329,36 +354,47 @@ __device__ __forceinline__ unsigned char *aligned_base(unsigned char *raw) {
 
 }  // namespace
 
-size_t tma_smem_bytes(int tb, bool two, bool cost) {
+size_t tma_smem_bytes(int tb, bool two, bool cost, int ns) {
   const size_t te = (size_t)1 << tb;
-  return 1024 + 2 * te * 8 * (two ? 2 : 1) + (cost ? 2 * te * 4 : 0) + 512 * 8 + 32 + 8 * 3 * 8;
+  return 1024 + ns * te * 8 * (two ? 2 : 1) + (cost ? ns * te * 4 : 0) + 512 * 8 + 32 + 8 * 3 * 8;
 }
 
 // ------------------------------------------------------------- forward
+//
+// NS = 2: 8 compute warps + 1 producer warp, two stages per CTA, one CTA per
+//         SM; the producer keeps the next tile's load in flight.
+// NS = 1: 8 compute warps, one stage per CTA, two CTAs per SM; thread 0
+//         issues the store and the next load between tiles, and the other
+//         CTA on the SM computes meanwhile.
 
-template <class PL>
-__global__ void __launch_bounds__(288, 1) k_fwd_tma(const __grid_constant__ TmaFwdParams P) {
-  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB;
+template <int NS> struct TmaCfg {
+  static constexpr int NT = NS == 1 ? 256 : 288;
+  static constexpr int MINB = NS == 1 ? 2 : 1;
+};
+
+template <class PL, int NS>
+__global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
+    k_fwd_tma(const __grid_constant__ TmaFwdParams P) {
+  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, NT = TmaCfg<NS>::NT;
   extern __shared__ unsigned char smem_raw[];
   const bool need_cost = P.has_phase || P.reduce;
   unsigned char *base = aligned_base(smem_raw);
-  const Lay L = layout(1u << PL::TB, false, need_cost);
+  const Lay L = layout(1u << PL::TB, false, need_cost, NS);
   float2 *tlo = reinterpret_cast<float2 *>(base + L.tab_off), *thi = tlo + 256;
   uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off), *empty = full + 2;
   double *red = reinterpret_cast<double *>(base + L.red_off);
   const int tid = threadIdx.x;
-  const uint32_t psi_bytes = L.tile_bytes, cost_bytes = L.cost_bytes;
   const int midbits = P.h - 4;
+  __shared__ int s_abort;
 
   if (P.has_phase && P.ph.mode == 0)
-    for (int i = tid; i < 256; i += 288) {
+    for (int i = tid; i < 256; i += NT) {
       tlo[i] = P.ph.tab_lo[i];
       thi[i] = P.ph.tab_hi[i];
     }
-  __shared__ int s_abort;
   if (tid == 0) {
     s_abort = 0;
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 256);
     }
@@ -366,30 +402,40 @@ __global__ void __launch_bounds__(288, 1) k_fwd_tma(const __grid_constant__ TmaF
   }
   __syncthreads();
 
-  if (tid >= 256) {
-    // ---------------- producer warp: TMA loads and stores
+  auto coords = [&](uint64_t T, int &c1, int &c4) {
+    c1 = (int)(T & ((1ull << midbits) - 1ull));
+    c4 = (int)(T >> midbits);
+  };
+  auto issue = [&](uint64_t T, int s) {
+    int c1, c4;
+    coords(T, c1, c4);
+    mbar_expect_tx(&full[s], (P.init_plus ? 0u : L.tile_bytes) + (need_cost ? L.cost_bytes : 0u));
+    if (!P.init_plus) tma_load(base + s * L.tile_bytes, &P.map_psi, c1, c4, &full[s]);
+    if (need_cost) tma_load(base + L.cost_off + s * L.cost_bytes, &P.map_cost, c1, c4, &full[s]);
+  };
+
+  if (tid == (NS == 1 ? 0 : 256))
+    for (int i = 0; i < NS; ++i) {
+      const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
+      if (T < P.ntiles) issue(T, i);
+    }
+
+  if (NS == 2 && tid >= 256) {
+    // ---------------- producer warp: stores of finished tiles, next loads
     if (tid == 256) {
-      auto issue = [&](uint64_t T, int s) {
-        const int c1 = (int)(T & ((1ull << midbits) - 1ull)), c4 = (int)(T >> midbits);
-        mbar_expect_tx(&full[s], (P.init_plus ? 0u : psi_bytes) + (need_cost ? cost_bytes : 0u));
-        if (!P.init_plus) tma_load(reinterpret_cast<float2 *>(base + s * L.tile_bytes), &P.map_psi, c1, c4, &full[s]);
-        if (need_cost) tma_load(reinterpret_cast<uint32_t *>(base + L.cost_off + s * L.cost_bytes), &P.map_cost, c1, c4, &full[s]);
-      };
-      for (int i = 0; i < 2; ++i) {
-        const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
-        if (T < P.ntiles) issue(T, i);
-      }
       for (int i = 0;; ++i) {
         const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
         if (T >= P.ntiles) break;
-        const int s = i & 1;
-        if (!mbar_wait(&empty[s], (i >> 1) & 1)) {
+        const int s = i % NS;
+        if (!mbar_wait(&empty[s], (i / NS) & 1)) {
           atomicExch(P.err, 1u);
           break;
         }
-        tma_store(&P.map_psi, reinterpret_cast<float2 *>(base + s * L.tile_bytes), (int)(T & ((1ull << midbits) - 1ull)), (int)(T >> midbits));
+        int c1, c4;
+        coords(T, c1, c4);
+        tma_store(&P.map_psi, base + s * L.tile_bytes, c1, c4);
         bulk_commit();
-        const uint64_t T2 = T + 2ull * gridDim.x;
+        const uint64_t T2 = T + (uint64_t)NS * gridDim.x;
         if (T2 < P.ntiles) {
           bulk_wait_read0();
           issue(T2, s);
@@ -404,17 +450,17 @@ __global__ void __launch_bounds__(288, 1) k_fwd_tma(const __grid_constant__ TmaF
     for (int i = 0;; ++i) {
       const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
       if (T >= P.ntiles) break;
-      const int s = i & 1;
+      const int s = i % NS;
       // every compute thread takes the same decision after a timeout, so no
       // thread is left waiting at a barrier the others skipped
-      if (!mbar_wait(&full[s], (i >> 1) & 1)) {
+      if (!mbar_wait(&full[s], (i / NS) & 1)) {
         s_abort = 1;
         atomicExch(P.err, 1u);
       }
       cbar();
       if (s_abort) break;
       float2 *buf = reinterpret_cast<float2 *>(base + s * L.tile_bytes);
-      const uint32_t *cb = reinterpret_cast<uint32_t *>(base + L.cost_off + s * L.cost_bytes);
+      const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off + s * L.cost_bytes);
       float2 v[NREG];
       if (P.init_plus) {
 #pragma unroll
@@ -424,36 +470,40 @@ __global__ void __launch_bounds__(288, 1) k_fwd_tma(const __grid_constant__ TmaF
       }
       bool final0;
       if (has1) {
-        rot_regs<EB>(v, P.s1.m[0], P.c1, P.s1s);
+        rot_tan<EB>(v, P.s1.m[0], P.tau1, P.form1);
         xp<PL, 0, 1>(v, buf);
-        rot_regs<EB>(v, P.s1.m[1], P.c1, P.s1s);
+        rot_tan<EB>(v, P.s1.m[1], P.tau1, P.form1);
         if constexpr (NR == 3) {
           xp<PL, 1, 2>(v, buf);
-          rot_regs<EB>(v, P.s1.m[2], P.c1, P.s1s);
+          rot_tan<EB>(v, P.s1.m[2], P.tau1, P.form1);
         }
-        if (P.has_phase) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tlo, thi);
+        if (P.has_phase) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
         if (has2) {
-          rot_regs<EB>(v, P.s2.m[NR - 1], P.c2, P.s2s);
+          rot_tan<EB>(v, P.s2.m[NR - 1], P.tau2, P.form2);
           if constexpr (NR == 3) {
             xp<PL, 2, 1>(v, buf);
-            rot_regs<EB>(v, P.s2.m[1], P.c2, P.s2s);
+            rot_tan<EB>(v, P.s2.m[1], P.tau2, P.form2);
           }
           xp<PL, 1, 0>(v, buf);
-          rot_regs<EB>(v, P.s2.m[0], P.c2, P.s2s);
+          rot_tan<EB>(v, P.s2.m[0], P.tau2, P.form2);
           final0 = true;
         } else {
           final0 = false;
         }
       } else {
-        if (P.has_phase) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tlo, thi);
-        rot_regs<EB>(v, P.s2.m[0], P.c2, P.s2s);
+        if (P.has_phase) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
+        rot_tan<EB>(v, P.s2.m[0], P.tau2, P.form2);
         xp<PL, 0, 1>(v, buf);
-        rot_regs<EB>(v, P.s2.m[1], P.c2, P.s2s);
+        rot_tan<EB>(v, P.s2.m[1], P.tau2, P.form2);
         if constexpr (NR == 3) {
           xp<PL, 1, 2>(v, buf);
-          rot_regs<EB>(v, P.s2.m[2], P.c2, P.s2s);
+          rot_tan<EB>(v, P.s2.m[2], P.tau2, P.form2);
         }
         final0 = false;
+      }
+      if (P.end_scale) {
+#pragma unroll
+        for (int r = 0; r < NREG; ++r) v[r] = cmulf(v[r], P.scl_end);
       }
       float e = 0.f, o = 0.f;
       if (final0) {
@@ -464,7 +514,22 @@ __global__ void __launch_bounds__(288, 1) k_fwd_tma(const __grid_constant__ TmaF
         sts_round<PL, NR - 1>(v, buf);
       }
       fence_async_smem();
-      mbar_arrive(&empty[s]);
+      if constexpr (NS == 2) {
+        mbar_arrive(&empty[s]);
+      } else {
+        cbar();
+        if (tid == 0) {
+          int c1, c4;
+          coords(T, c1, c4);
+          tma_store(&P.map_psi, buf, c1, c4);
+          bulk_commit();
+          const uint64_t T2 = T + gridDim.x;
+          if (T2 < P.ntiles) {
+            bulk_wait_read0();
+            issue(T2, 0);
+          }
+        }
+      }
       if (P.reduce) {
         double a[2] = {(double)e, (double)o};
         csum<2>(a, red);
@@ -474,6 +539,7 @@ __global__ void __launch_bounds__(288, 1) k_fwd_tma(const __grid_constant__ TmaF
         }
       }
     }
+    if (NS == 1 && tid == 0) bulk_wait0();
   }
   if (P.reduce) {
     double *out = P.out;
@@ -486,29 +552,29 @@ __global__ void __launch_bounds__(288, 1) k_fwd_tma(const __grid_constant__ TmaF
 
 // ------------------------------------------------------------- adjoint
 
-template <class PL>
-__global__ void __launch_bounds__(288, 1) k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
-  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB;
+template <class PL, int NS>
+__global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
+    k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
+  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, NT = TmaCfg<NS>::NT;
   extern __shared__ unsigned char smem_raw[];
   const bool need_cost = P.has_phase || P.init_lambda;
   unsigned char *base = aligned_base(smem_raw);
-  const Lay L = layout(1u << PL::TB, true, need_cost);
+  const Lay L = layout(1u << PL::TB, true, need_cost, NS);
   float2 *tlo = reinterpret_cast<float2 *>(base + L.tab_off), *thi = tlo + 256;
   uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off), *empty = full + 2;
   double *red = reinterpret_cast<double *>(base + L.red_off);
   const int tid = threadIdx.x;
-  const uint32_t vec_bytes = L.tile_bytes, cost_bytes = L.cost_bytes;
   const int midbits = P.h - 4;
+  __shared__ int s_abort;
 
   if (P.has_phase && P.ph.mode == 0)
-    for (int i = tid; i < 256; i += 288) {
+    for (int i = tid; i < 256; i += NT) {
       tlo[i] = P.ph.tab_lo[i];
       thi[i] = P.ph.tab_hi[i];
     }
-  __shared__ int s_abort;
   if (tid == 0) {
     s_abort = 0;
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 256);
     }
@@ -516,33 +582,45 @@ __global__ void __launch_bounds__(288, 1) k_bwd_tma(const __grid_constant__ TmaB
   }
   __syncthreads();
 
-  if (tid >= 256) {
+  auto coords = [&](uint64_t T, int &c1, int &c4) {
+    c1 = (int)(T & ((1ull << midbits) - 1ull));
+    c4 = (int)(T >> midbits);
+  };
+  auto issue = [&](uint64_t T, int s) {
+    int c1, c4;
+    coords(T, c1, c4);
+    mbar_expect_tx(&full[s], L.tile_bytes + (P.init_lambda ? 0u : L.tile_bytes) +
+                                 (need_cost ? L.cost_bytes : 0u));
+    tma_load(base + s * L.tile_bytes, &P.map_psi, c1, c4, &full[s]);
+    if (!P.init_lambda) tma_load(base + L.lam_off + s * L.tile_bytes, &P.map_lam, c1, c4, &full[s]);
+    if (need_cost) tma_load(base + L.cost_off + s * L.cost_bytes, &P.map_cost, c1, c4, &full[s]);
+  };
+  auto store = [&](uint64_t T, int s) {
+    int c1, c4;
+    coords(T, c1, c4);
+    tma_store(&P.map_psi, base + s * L.tile_bytes, c1, c4);
+    tma_store(&P.map_lam, base + L.lam_off + s * L.tile_bytes, c1, c4);
+    bulk_commit();
+  };
+
+  if (tid == (NS == 1 ? 0 : 256))
+    for (int i = 0; i < NS; ++i) {
+      const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
+      if (T < P.ntiles) issue(T, i);
+    }
+
+  if (NS == 2 && tid >= 256) {
     if (tid == 256) {
-      auto issue = [&](uint64_t T, int s) {
-        const int c1 = (int)(T & ((1ull << midbits) - 1ull)), c4 = (int)(T >> midbits);
-        mbar_expect_tx(&full[s], vec_bytes + (P.init_lambda ? 0u : vec_bytes) +
-                                       (need_cost ? cost_bytes : 0u));
-        tma_load(reinterpret_cast<float2 *>(base + s * L.tile_bytes), &P.map_psi, c1, c4, &full[s]);
-        if (!P.init_lambda) tma_load(reinterpret_cast<float2 *>(base + L.lam_off + s * L.tile_bytes), &P.map_lam, c1, c4, &full[s]);
-        if (need_cost) tma_load(reinterpret_cast<uint32_t *>(base + L.cost_off + s * L.cost_bytes), &P.map_cost, c1, c4, &full[s]);
-      };
-      for (int i = 0; i < 2; ++i) {
-        const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
-        if (T < P.ntiles) issue(T, i);
-      }
       for (int i = 0;; ++i) {
         const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
         if (T >= P.ntiles) break;
-        const int s = i & 1;
-        if (!mbar_wait(&empty[s], (i >> 1) & 1)) {
+        const int s = i % NS;
+        if (!mbar_wait(&empty[s], (i / NS) & 1)) {
           atomicExch(P.err, 1u);
           break;
         }
-        const int c1 = (int)(T & ((1ull << midbits) - 1ull)), c4 = (int)(T >> midbits);
-        tma_store(&P.map_psi, reinterpret_cast<float2 *>(base + s * L.tile_bytes), c1, c4);
-        tma_store(&P.map_lam, reinterpret_cast<float2 *>(base + L.lam_off + s * L.tile_bytes), c1, c4);
-        bulk_commit();
-        const uint64_t T2 = T + 2ull * gridDim.x;
+        store(T, s);
+        const uint64_t T2 = T + (uint64_t)NS * gridDim.x;
         if (T2 < P.ntiles) {
           bulk_wait_read0();
           issue(T2, s);
@@ -555,17 +633,16 @@ __global__ void __launch_bounds__(288, 1) k_bwd_tma(const __grid_constant__ TmaB
     for (int i = 0;; ++i) {
       const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
       if (T >= P.ntiles) break;
-      const int s = i & 1;
-      // every compute thread takes the same decision after a timeout, so no
-      // thread is left waiting at a barrier the others skipped
-      if (!mbar_wait(&full[s], (i >> 1) & 1)) {
+      const int s = i % NS;
+      if (!mbar_wait(&full[s], (i / NS) & 1)) {
         s_abort = 1;
         atomicExch(P.err, 1u);
       }
       cbar();
       if (s_abort) break;
-      float2 *bv = reinterpret_cast<float2 *>(base + s * L.tile_bytes), *bw = reinterpret_cast<float2 *>(base + L.lam_off + s * L.tile_bytes);
-      const uint32_t *cb = reinterpret_cast<uint32_t *>(base + L.cost_off + s * L.cost_bytes);
+      float2 *bv = reinterpret_cast<float2 *>(base + s * L.tile_bytes);
+      float2 *bw = reinterpret_cast<float2 *>(base + L.lam_off + s * L.tile_bytes);
+      const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off + s * L.cost_bytes);
       float2 v[NREG], w[NREG];
       lds_round<PL, 0>(v, bv);
       if (P.init_lambda) {
@@ -580,20 +657,20 @@ __global__ void __launch_bounds__(288, 1) k_bwd_tma(const __grid_constant__ TmaB
         lds_round<PL, 0>(w, bw);
       }
       float a1 = 0.f, ag = 0.f, a2 = 0.f;
-      unrot_acc<EB>(v, w, P.s1.m[0], P.c1, P.s1s, a1);
+      unrot_tan<EB>(v, w, P.s1.m[0], P.tau1, P.form1, P.w1[0], a1);
       sts_round<PL, 0>(v, bv);
       sts_round<PL, 0>(w, bw);
       cbar();
       lds_round<PL, 1>(v, bv);
       lds_round<PL, 1>(w, bw);
-      unrot_acc<EB>(v, w, P.s1.m[1], P.c1, P.s1s, a1);
+      unrot_tan<EB>(v, w, P.s1.m[1], P.tau1, P.form1, P.w1[1], a1);
       if constexpr (NR == 3) {
         sts_round<PL, 1>(v, bv);
         sts_round<PL, 1>(w, bw);
         cbar();
         lds_round<PL, 2>(v, bv);
         lds_round<PL, 2>(w, bw);
-        unrot_acc<EB>(v, w, P.s1.m[2], P.c1, P.s1s, a1);
+        unrot_tan<EB>(v, w, P.s1.m[2], P.tau1, P.form1, P.w1[2], a1);
       }
       if (P.has_phase) {
         // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
@@ -602,29 +679,30 @@ __global__ void __launch_bounds__(288, 1) k_bwd_tma(const __grid_constant__ TmaB
         for (int r = 0; r < NREG; ++r) {
           const uint32_t word = cb[tt | pdep(r, PL::reg(NR - 1))];
           const float f = cost_val(P.cost_kind, word);
-          ag += f * (w[r].x * v[r].y - w[r].y * v[r].x);
-          const float2 ph = phase_of(P.ph, P.cost_kind, tlo, thi, word);
+          ag += P.wg * f * (w[r].x * v[r].y - w[r].y * v[r].x);
+          float2 ph = phase_of(P.ph, P.cost_kind, tlo, thi, word);
+          if (P.ph.mode != 0) ph = cmulf(ph, P.scl_phase);
           v[r] = cmulf(v[r], ph);
           w[r] = cmulf(w[r], ph);
         }
       }
       bool final0 = false;
       if (has2) {
-        unrot_acc<EB>(v, w, P.s2.m[NR - 1], P.c2, P.s2s, a2);
+        unrot_tan<EB>(v, w, P.s2.m[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
         if constexpr (NR == 3) {
           sts_round<PL, 2>(v, bv);
           sts_round<PL, 2>(w, bw);
           cbar();
           lds_round<PL, 1>(v, bv);
           lds_round<PL, 1>(w, bw);
-          unrot_acc<EB>(v, w, P.s2.m[1], P.c2, P.s2s, a2);
+          unrot_tan<EB>(v, w, P.s2.m[1], P.tau2, P.form2, P.w2[1], a2);
         }
         sts_round<PL, 1>(v, bv);
         sts_round<PL, 1>(w, bw);
         cbar();
         lds_round<PL, 0>(v, bv);
         lds_round<PL, 0>(w, bw);
-        unrot_acc<EB>(v, w, P.s2.m[0], P.c2, P.s2s, a2);
+        unrot_tan<EB>(v, w, P.s2.m[0], P.tau2, P.form2, P.w2[0], a2);
         final0 = true;
       }
       if (final0) {
@@ -635,7 +713,19 @@ __global__ void __launch_bounds__(288, 1) k_bwd_tma(const __grid_constant__ TmaB
         sts_round<PL, NR - 1>(w, bw);
       }
       fence_async_smem();
-      mbar_arrive(&empty[s]);
+      if constexpr (NS == 2) {
+        mbar_arrive(&empty[s]);
+      } else {
+        cbar();
+        if (tid == 0) {
+          store(T, 0);
+          const uint64_t T2 = T + gridDim.x;
+          if (T2 < P.ntiles) {
+            bulk_wait_read0();
+            issue(T2, 0);
+          }
+        }
+      }
       double a[3] = {(double)a1, (double)ag, (double)a2};
       csum<3>(a, red);
       if (tid == 0) {
@@ -644,6 +734,7 @@ __global__ void __launch_bounds__(288, 1) k_bwd_tma(const __grid_constant__ TmaB
         P.partials[T * 3 + 2] = a[2];
       }
     }
+    if (NS == 1 && tid == 0) bulk_wait0();
   }
   double *o1 = P.out_b1, *og = P.out_g, *o2 = P.out_b2;
   final_reduce<3>(P.partials, P.ntiles, P.counter, red, [=](double(&a)[3]) {
@@ -696,42 +787,58 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <class PL>
+template <class PL, int NS>
 static cudaError_t launch_fwd_tma_t(const TmaFwdParams &P, cudaStream_t s, int nsm) {
-  const size_t smem = tma_smem_bytes(PL::TB, false, P.has_phase || P.reduce);
-  static bool init = false;
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(k_fwd_tma<PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tma_smem_bytes(PL::TB, false, true));
+  const size_t smem = tma_smem_bytes(PL::TB, false, P.has_phase || P.reduce, NS);
+  auto kern = k_fwd_tma<PL, NS>;
+  static int nb = 0;
+  if (nb == 0) {
+    const size_t mx = tma_smem_bytes(PL::TB, false, true, NS);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e != cudaSuccess) return e;
-    init = true;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TmaCfg<NS>::NT, mx) != cudaSuccess || b < 1) b = 1;
+    nb = b;
   }
-  const uint64_t grid = P.ntiles < (uint64_t)nsm ? P.ntiles : (uint64_t)nsm;
-  k_fwd_tma<PL><<<(unsigned)grid, 288, smem, s>>>(P);
+  uint64_t grid = (uint64_t)nsm * nb;
+  if (grid > P.ntiles) grid = P.ntiles;
+  kern<<<(unsigned)grid, TmaCfg<NS>::NT, smem, s>>>(P);
   return cudaGetLastError();
 }
 
-template <class PL>
+template <class PL, int NS>
 static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int nsm) {
-  const size_t smem = tma_smem_bytes(PL::TB, true, P.has_phase || P.init_lambda);
-  static bool init = false;
-  if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(k_bwd_tma<PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tma_smem_bytes(PL::TB, true, true));
+  const size_t smem = tma_smem_bytes(PL::TB, true, P.has_phase || P.init_lambda, NS);
+  auto kern = k_bwd_tma<PL, NS>;
+  static int nb = 0;
+  if (nb == 0) {
+    const size_t mx = tma_smem_bytes(PL::TB, true, true, NS);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e != cudaSuccess) return e;
-    init = true;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TmaCfg<NS>::NT, mx) != cudaSuccess || b < 1) b = 1;
+    nb = b;
   }
-  const uint64_t grid = P.ntiles < (uint64_t)nsm ? P.ntiles : (uint64_t)nsm;
-  k_bwd_tma<PL><<<(unsigned)grid, 288, smem, s>>>(P);
+  uint64_t grid = (uint64_t)nsm * nb;
+  if (grid > P.ntiles) grid = P.ntiles;
+  kern<<<(unsigned)grid, TmaCfg<NS>::NT, smem, s>>>(P);
   return cudaGetLastError();
 }
+
+#ifndef QAOA_TMA_STAGES
+#define QAOA_TMA_STAGES 1
+#endif
 
 cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm) {
-  return high ? launch_fwd_tma_t<PlanTmaF13High>(P, s, nsm) : launch_fwd_tma_t<PlanTmaF13Low>(P, s, nsm);
+  constexpr int NS = QAOA_TMA_STAGES;
+  return high ? launch_fwd_tma_t<PlanTmaF13High, NS>(P, s, nsm)
+              : launch_fwd_tma_t<PlanTmaF13Low, NS>(P, s, nsm);
 }
 
 cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {
-  return high ? launch_bwd_tma_t<PlanTmaB12High>(P, s, nsm) : launch_bwd_tma_t<PlanTmaB12Low>(P, s, nsm);
+  constexpr int NS = QAOA_TMA_STAGES;
+  return high ? launch_bwd_tma_t<PlanTmaB12High, NS>(P, s, nsm)
+              : launch_bwd_tma_t<PlanTmaB12Low, NS>(P, s, nsm);
 }
 
 }  // namespace qaoa
