@@ -140,28 +140,41 @@ void make_phase(PhaseData<Real> &ph, double g, qaoa_cost_type ct, const qaoa_cos
   }
 }
 
-// Rotation schedule of one sweep over the tile bits in `set`.
+// Rotation schedule of one sweep over the tile bits in `set`: each bit goes
+// to the first round (in the kernel's traversal order) holding it in a
+// register; bits no round holds in a register go to the first round holding
+// them in a lane (rotated with a warp shuffle; TMA kernels only).
 template <class PL>
 Sweep make_sweep(uint32_t set, bool ascending) {
   Sweep s;
   memset(&s, 0, sizeof(s));
-  uint32_t done = 0;
-  for (int k = 0; k < PL::NR; ++k) {
-    const int r = ascending ? k : PL::NR - 1 - k;
-    const uint32_t regs = PL::reg(r);
-    const uint32_t m = regs & set & ~done;
-    done |= m;
+  auto compress = [](uint32_t m, uint32_t within) {
     uint8_t bits = 0;
     int i = 0;
     for (int b = 0; b < 32; ++b)
-      if ((regs >> b) & 1u) {
+      if ((within >> b) & 1u) {
         if ((m >> b) & 1u) bits |= (uint8_t)(1u << i);
         ++i;
       }
-    s.m[r] = bits;
+    return bits;
+  };
+  uint32_t done = 0;
+  for (int k = 0; k < PL::NR; ++k) {
+    const int r = ascending ? k : PL::NR - 1 - k;
+    const uint32_t m = PL::reg(r) & set & ~done;
+    done |= m;
+    s.m[r] = compress(m, PL::reg(r));
+  }
+  for (int k = 0; k < PL::NR; ++k) {
+    const int r = ascending ? k : PL::NR - 1 - k;
+    const uint32_t m = PL::lane(r) & set & ~done;
+    done |= m;
+    s.lm[r] = compress(m, PL::lane(r));
   }
   return s;
 }
+
+bool uses_lanes(const Sweep &s) { return (s.lm[0] | s.lm[1] | s.lm[2] | s.lm[3]) != 0; }
 
 struct Group {
   bool high;
@@ -169,20 +182,21 @@ struct Group {
   uint32_t rot;      // tile bits rotated
 };
 
-// LOW group + HIGH groups covering qubits [TB, n) (TB - 4 per pass).
-std::vector<Group> plan_groups(int n, int TB) {
+// LOW group + HIGH groups covering qubits [TB, n), TB - chigh per pass
+// (chigh passenger bits keep every global segment 2^chigh amplitudes long).
+std::vector<Group> plan_groups(int n, int TB, int chigh = kHighC) {
   std::vector<Group> gs;
   gs.push_back(Group{false, TB, TB, (1u << TB) - 1u});
-  const int span = TB - kHighC;
+  const int span = TB - chigh;
   for (int q0 = TB; q0 < n;) {
     const int len = (n - q0) < span ? (n - q0) : span;
     const int h = q0 < n - span ? q0 : n - span;
     uint32_t rot = 0;
-    for (int j = kHighC; j < TB; ++j) {
-      const int xb = h + j - kHighC;
+    for (int j = chigh; j < TB; ++j) {
+      const int xb = h + j - chigh;
       if (xb >= q0 && xb < q0 + len) rot |= 1u << j;
     }
-    gs.push_back(Group{true, kHighC, h, rot});
+    gs.push_back(Group{true, chigh, h, rot});
     q0 += len;
   }
   return gs;
@@ -385,6 +399,7 @@ qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa
     P.cost_kind = cost_kind(ct);
     P.g = make_geom(n, G, TB);
     const bool two = op.l1 >= 0 && op.l2 >= 0;  // both sweeps: s1 ascends, s2 descends
+    // (these plans hold every rotated bit in registers: no lane rotations)
     if (op.l1 >= 0) {
       P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
       P.c1 = (Real)cos(bet[op.l1]);
@@ -395,6 +410,7 @@ qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa
       P.c2 = (Real)cos(bet[op.l2]);
       P.s2s = (Real)sin(bet[op.l2]);
     }
+    if (uses_lanes(P.s1) || uses_lanes(P.s2)) return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
     P.has_phase = op.lp >= 0;
     if (P.has_phase) make_phase<Real>(P.ph, gam[op.lp], ct, stats);
     P.init_plus = op.init;
@@ -451,6 +467,7 @@ qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qao
       P.s2s = (Real)-sin(bet[op.l2]);
       P.out_b2 = d_grad_b + op.l2;
     }
+    if (uses_lanes(P.s1) || uses_lanes(P.s2)) return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
     P.init_lambda = op.init;
     P.partials = ws.partials;
     P.counter = ws.counter;
@@ -513,11 +530,12 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
   for (const PassOp &op : ops) {
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
-    const int h = G.high ? G.h : 4;
-    CK(make_tile_map(&P.map_psi, state, n, TB, h, 8, true), "tensor map (state)");
-    CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, 4, false), "tensor map (cost)");
+    const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
+    CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, c == 4 ? 128 : 64), "tensor map (state)");
+    CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, 4, 0), "tensor map (cost)");
     P.ntiles = 1ull << (n - TB);
     P.h = h;
+    P.c = c;
     P.cost_kind = cost_kind(ct);
     const bool two = op.l1 >= 0 && op.l2 >= 0;
     const int nrot = __builtin_popcount(G.rot);
@@ -571,7 +589,8 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
   using Low = PlanTmaB12Low;
   using High = PlanTmaB12High;
   const int TB = Low::TB;
-  const std::vector<Group> gs = plan_groups(n, TB);
+  // 16-amplitude (128-byte) segments: 8-amplitude ones halve the HBM efficiency
+  const std::vector<Group> gs = plan_groups(n, TB, kHighC);
   const std::vector<PassOp> ops = adjoint_schedule((int)gs.size(), p);
   const int nsm = num_sms();
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
@@ -582,12 +601,14 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
   for (const PassOp &op : ops) {
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
-    const int h = G.high ? G.h : 4;
-    CK(make_tile_map(&P.map_psi, state, n, TB, h, 8, true), "tensor map (psi)");
-    CK(make_tile_map(&P.map_lam, lam, n, TB, h, 8, true), "tensor map (lambda)");
-    CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, 4, false), "tensor map (cost)");
+    const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
+    const int sw = c == 4 ? 128 : 64;
+    CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, sw), "tensor map (psi)");
+    CK(make_tile_map(&P.map_lam, lam, n, TB, h, c, 8, sw), "tensor map (lambda)");
+    CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, 4, 0), "tensor map (cost)");
     P.ntiles = 1ull << (n - TB);
     P.h = h;
+    P.c = c;
     P.cost_kind = cost_kind(ct);
     P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
     {
@@ -598,7 +619,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
       // product is the true one divided by |sig|^2
       for (int r = 0; r < Low::NR; ++r) {  // the kernel walks s1 upward
         P.w1[r] = (float)std::norm(sig);
-        sig *= std::pow(R.sigma, popc8(P.s1.m[r]));
+        sig *= std::pow(R.sigma, popc8(P.s1.m[r]) + popc8(P.s1.lm[r]));
       }
     }
     P.out_b1 = d_grad_b + op.l1;
@@ -619,7 +640,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
       for (int k = 0; k < Low::NR; ++k) {  // and s2 downward
         const int r = Low::NR - 1 - k;
         P.w2[r] = (float)std::norm(sig);
-        sig *= std::pow(R.sigma, popc8(P.s2.m[r]));
+        sig *= std::pow(R.sigma, popc8(P.s2.m[r]) + popc8(P.s2.lm[r]));
       }
       P.out_b2 = d_grad_b + op.l2;
     }

@@ -76,7 +76,7 @@ struct alignas(64) TmaFwdParams {
   CUtensorMap map_psi;   // state, 8-byte elements, 128-byte swizzle
   CUtensorMap map_cost;  // cost vector, 4-byte elements
   uint64_t ntiles;
-  int h, cost_kind;
+  int h, c, cost_kind;  // tile = 2^c contiguous amplitudes x rows at qubits h..
   Sweep s1, s2;
   float tau1, tau2;
   int form1, form2;
@@ -95,7 +95,7 @@ struct alignas(64) TmaFwdParams {
 struct alignas(64) TmaBwdParams {
   CUtensorMap map_psi, map_lam, map_cost;
   uint64_t ntiles;
-  int h, cost_kind;
+  int h, c, cost_kind;
   Sweep s1, s2;
   float tau1, tau2;
   int form1, form2;
@@ -110,7 +110,8 @@ struct alignas(64) TmaBwdParams {
   PhaseData<float> ph;
 };
 
-cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, int esz, bool swizzle);
+cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, int c, int esz,
+                          int swizzle_bytes);
 cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm);
 cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm);
 

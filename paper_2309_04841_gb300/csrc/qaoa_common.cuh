@@ -114,9 +114,11 @@ __device__ __forceinline__ uint64_t tile_off(const Geom &g, uint32_t t) {
 }
 
 // Rotation schedule of one sweep: for round r, bit i of m[r] says "rotate
-// register bit i in this round".
+// register bit i in this round" and bit i of lm[r] "rotate the tile bit held
+// by lane-index bit i, with a warp shuffle" (TMA kernels only).
 struct Sweep {
   uint8_t m[4];
+  uint8_t lm[4];
 };
 
 // ------------------------------------------------------------ parameters

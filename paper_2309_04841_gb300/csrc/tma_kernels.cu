@@ -103,9 +103,13 @@ __device__ __forceinline__ void fence_mbar_init() {
 // Barrier among the 256 compute threads only (the producer warp never joins).
 __device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-// TMA SWIZZLE_128B seen at 8-byte granularity: the 16-byte chunk index inside
-// each 128-byte row is XORed with the row index mod 8.
-__host__ __device__ constexpr uint32_t tswz(uint32_t t) { return t ^ (((t >> 4) & 7u) << 1); }
+// TMA swizzle seen at 8-byte granularity.  SWIZZLE_128B: the 16-byte chunk
+// index inside each 128-byte row is XORed with the row index mod 8;
+// SWIZZLE_64B: bits 4-5 of the byte address are XORed with bits 7-8.
+template <int SW>
+__host__ __device__ constexpr uint32_t tswz(uint32_t t) {
+  return SW == 128 ? t ^ (((t >> 4) & 7u) << 1) : t ^ (((t >> 4) & 3u) << 1);
+}
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
@@ -142,13 +146,31 @@ __device__ __forceinline__ void rot_tan(float2 (&v)[1 << EB], uint32_t m, float 
   }
 }
 
+// Reduced-form rotation of the tile bits held by the lane-index bits in lm:
+// the partner amplitude comes from lane ^ 2^b by a warp shuffle.  The gate is
+// symmetric in (a, b), so both lanes apply the same update to their own value.
+template <int N>
+__device__ __forceinline__ void rot_lanes(float2 (&v)[N], uint32_t lm, float tau, int form) {
+#pragma unroll
+  for (int b = 0; b < 5; ++b)
+    if ((lm >> b) & 1u) {
+#pragma unroll
+      for (int r = 0; r < N; ++r) {
+        const float px = __shfl_xor_sync(0xffffffffu, v[r].x, 1 << b);
+        const float py = __shfl_xor_sync(0xffffffffu, v[r].y, 1 << b);
+        v[r] = form == 0 ? f2(fmaf(tau, py, v[r].x), fmaf(-tau, px, v[r].y))
+                         : f2(fmaf(-tau, v[r].y, px), fmaf(tau, v[r].x, py));
+      }
+    }
+}
+
 // Adjoint: reduced-form un-rotation of psi (v) and lambda (w), adding the raw
 // Im <lambda| X_q |psi> of each pair first; the round's sum is weighted by wr
 // (the squared scale the stored vectors owe at this point).
 template <int EB>
 __device__ __forceinline__ void unrot_tan(float2 (&v)[1 << EB], float2 (&w)[1 << EB], uint32_t m,
-                                          float tau, int form, float wr, float &acc) {
-  if (m == 0u) return;
+                                          uint32_t lm, float tau, int form, float wr, float &acc) {
+  if ((m | lm) == 0u) return;
   float racc = 0.f;
 #pragma unroll
   for (int i = 0; i < EB; ++i)
@@ -160,9 +182,23 @@ __device__ __forceinline__ void unrot_tan(float2 (&v)[1 << EB], float2 (&w)[1 <<
           racc += la.x * pb.y - la.y * pb.x + lb.x * pa.y - lb.y * pa.x;
         }
     }
+#pragma unroll
+  for (int b = 0; b < 5; ++b)
+    if ((lm >> b) & 1u) {
+      // each lane adds Im(conj(lambda_self) psi_partner): the pair's two terms
+      // come from its two lanes
+#pragma unroll
+      for (int r = 0; r < (1 << EB); ++r) {
+        const float px = __shfl_xor_sync(0xffffffffu, v[r].x, 1 << b);
+        const float py = __shfl_xor_sync(0xffffffffu, v[r].y, 1 << b);
+        racc += w[r].x * py - w[r].y * px;
+      }
+    }
   acc = fmaf(racc, wr, acc);
   rot_tan<EB>(v, m, tau, form);
   rot_tan<EB>(w, m, tau, form);
+  rot_lanes<(1 << EB)>(v, lm, tau, form);
+  rot_lanes<(1 << EB)>(w, lm, tau, form);
 }
 
 __device__ __forceinline__ uint32_t pdep_d(uint32_t v, uint32_t mask) {
@@ -185,41 +221,41 @@ __device__ __forceinline__ uint32_t thr_tile() {
 
 // Registers <- shared tile in round-R layout (16-byte accesses when the
 // round holds tile bit 0 in registers).
-template <class PL, int R>
+template <class PL, int R, int SW>
 __device__ __forceinline__ void lds_round(float2 (&v)[PL::NREG], const float2 *buf) {
-  const uint32_t st = tswz(thr_tile<PL, R>());
+  const uint32_t st = tswz<SW>(thr_tile<PL, R>());
   if constexpr ((PL::reg(R) & 1u) != 0u) {
 #pragma unroll
     for (int r = 0; r < PL::NREG; r += 2) {
-      const float4 q = *reinterpret_cast<const float4 *>(buf + (st ^ tswz(pdep(r, PL::reg(R)))));
+      const float4 q = *reinterpret_cast<const float4 *>(buf + (st ^ tswz<SW>(pdep(r, PL::reg(R)))));
       v[r] = f2(q.x, q.y);
       v[r + 1] = f2(q.z, q.w);
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < PL::NREG; ++r) v[r] = buf[st ^ tswz(pdep(r, PL::reg(R)))];
+    for (int r = 0; r < PL::NREG; ++r) v[r] = buf[st ^ tswz<SW>(pdep(r, PL::reg(R)))];
   }
 }
 
-template <class PL, int R>
+template <class PL, int R, int SW>
 __device__ __forceinline__ void sts_round(const float2 (&v)[PL::NREG], float2 *buf) {
-  const uint32_t st = tswz(thr_tile<PL, R>());
+  const uint32_t st = tswz<SW>(thr_tile<PL, R>());
   if constexpr ((PL::reg(R) & 1u) != 0u) {
 #pragma unroll
     for (int r = 0; r < PL::NREG; r += 2)
-      *reinterpret_cast<float4 *>(buf + (st ^ tswz(pdep(r, PL::reg(R))))) =
+      *reinterpret_cast<float4 *>(buf + (st ^ tswz<SW>(pdep(r, PL::reg(R))))) =
           make_float4(v[r].x, v[r].y, v[r + 1].x, v[r + 1].y);
   } else {
 #pragma unroll
-    for (int r = 0; r < PL::NREG; ++r) buf[st ^ tswz(pdep(r, PL::reg(R)))] = v[r];
+    for (int r = 0; r < PL::NREG; ++r) buf[st ^ tswz<SW>(pdep(r, PL::reg(R)))] = v[r];
   }
 }
 
-template <class PL, int RF, int RT>
+template <class PL, int RF, int RT, int SW>
 __device__ __forceinline__ void xp(float2 (&v)[PL::NREG], float2 *buf) {
-  sts_round<PL, RF>(v, buf);
+  sts_round<PL, RF, SW>(v, buf);
   cbar();
-  lds_round<PL, RT>(v, buf);
+  lds_round<PL, RT, SW>(v, buf);
 }
 
 // exp(-i g f) from the raw 32-bit cost word (int32 or float32).
@@ -372,7 +408,7 @@ template <int NS> struct TmaCfg {
   static constexpr int MINB = NS == 1 ? 2 : 1;
 };
 
-template <class PL, int NS>
+template <class PL, int NS, int SW>
 __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     k_fwd_tma(const __grid_constant__ TmaFwdParams P) {
   constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, NT = TmaCfg<NS>::NT;
@@ -384,7 +420,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
   uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off), *empty = full + 2;
   double *red = reinterpret_cast<double *>(base + L.red_off);
   const int tid = threadIdx.x;
-  const int midbits = P.h - 4;
+  const int midbits = P.h - P.c;
   __shared__ int s_abort;
 
   if (P.has_phase && P.ph.mode == 0)
@@ -445,8 +481,8 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     }
   } else {
     // ---------------- compute warps
-    const bool has1 = (P.s1.m[0] | P.s1.m[1] | P.s1.m[2]) != 0;
-    const bool has2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2]) != 0;
+    const bool has1 = (P.s1.m[0] | P.s1.m[1] | P.s1.m[2] | P.s1.lm[0] | P.s1.lm[1] | P.s1.lm[2]) != 0;
+    const bool has2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2] | P.s2.lm[0] | P.s2.lm[1] | P.s2.lm[2]) != 0;
     for (int i = 0;; ++i) {
       const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
       if (T >= P.ntiles) break;
@@ -466,26 +502,32 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
 #pragma unroll
         for (int r = 0; r < NREG; ++r) v[r] = f2(P.amp, 0.f);
       } else {
-        lds_round<PL, 0>(v, buf);
+        lds_round<PL, 0, SW>(v, buf);
       }
       bool final0;
       if (has1) {
         rot_tan<EB>(v, P.s1.m[0], P.tau1, P.form1);
-        xp<PL, 0, 1>(v, buf);
+        rot_lanes<NREG>(v, P.s1.lm[0], P.tau1, P.form1);
+        xp<PL, 0, 1, SW>(v, buf);
         rot_tan<EB>(v, P.s1.m[1], P.tau1, P.form1);
+        rot_lanes<NREG>(v, P.s1.lm[1], P.tau1, P.form1);
         if constexpr (NR == 3) {
-          xp<PL, 1, 2>(v, buf);
+          xp<PL, 1, 2, SW>(v, buf);
           rot_tan<EB>(v, P.s1.m[2], P.tau1, P.form1);
+        rot_lanes<NREG>(v, P.s1.lm[2], P.tau1, P.form1);
         }
         if (P.has_phase) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
         if (has2) {
           rot_tan<EB>(v, P.s2.m[NR - 1], P.tau2, P.form2);
+        rot_lanes<NREG>(v, P.s2.lm[NR - 1], P.tau2, P.form2);
           if constexpr (NR == 3) {
-            xp<PL, 2, 1>(v, buf);
+            xp<PL, 2, 1, SW>(v, buf);
             rot_tan<EB>(v, P.s2.m[1], P.tau2, P.form2);
+        rot_lanes<NREG>(v, P.s2.lm[1], P.tau2, P.form2);
           }
-          xp<PL, 1, 0>(v, buf);
+          xp<PL, 1, 0, SW>(v, buf);
           rot_tan<EB>(v, P.s2.m[0], P.tau2, P.form2);
+        rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
           final0 = true;
         } else {
           final0 = false;
@@ -493,11 +535,14 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       } else {
         if (P.has_phase) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
         rot_tan<EB>(v, P.s2.m[0], P.tau2, P.form2);
-        xp<PL, 0, 1>(v, buf);
+        rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
+        xp<PL, 0, 1, SW>(v, buf);
         rot_tan<EB>(v, P.s2.m[1], P.tau2, P.form2);
+        rot_lanes<NREG>(v, P.s2.lm[1], P.tau2, P.form2);
         if constexpr (NR == 3) {
-          xp<PL, 1, 2>(v, buf);
+          xp<PL, 1, 2, SW>(v, buf);
           rot_tan<EB>(v, P.s2.m[2], P.tau2, P.form2);
+        rot_lanes<NREG>(v, P.s2.lm[2], P.tau2, P.form2);
         }
         final0 = false;
       }
@@ -508,10 +553,10 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       float e = 0.f, o = 0.f;
       if (final0) {
         if (P.reduce) eo_round<PL, 0>(v, cb, P.cost_kind, P.fmin_d, e, o);
-        sts_round<PL, 0>(v, buf);
+        sts_round<PL, 0, SW>(v, buf);
       } else {
         if (P.reduce) eo_round<PL, NR - 1>(v, cb, P.cost_kind, P.fmin_d, e, o);
-        sts_round<PL, NR - 1>(v, buf);
+        sts_round<PL, NR - 1, SW>(v, buf);
       }
       fence_async_smem();
       if constexpr (NS == 2) {
@@ -552,7 +597,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
 
 // ------------------------------------------------------------- adjoint
 
-template <class PL, int NS>
+template <class PL, int NS, int SW>
 __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
   constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, NT = TmaCfg<NS>::NT;
@@ -564,7 +609,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
   uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off), *empty = full + 2;
   double *red = reinterpret_cast<double *>(base + L.red_off);
   const int tid = threadIdx.x;
-  const int midbits = P.h - 4;
+  const int midbits = P.h - P.c;
   __shared__ int s_abort;
 
   if (P.has_phase && P.ph.mode == 0)
@@ -629,7 +674,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       bulk_wait0();
     }
   } else {
-    const bool has2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2]) != 0;
+    const bool has2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2] | P.s2.lm[0] | P.s2.lm[1] | P.s2.lm[2]) != 0;
     for (int i = 0;; ++i) {
       const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
       if (T >= P.ntiles) break;
@@ -644,7 +689,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       float2 *bw = reinterpret_cast<float2 *>(base + L.lam_off + s * L.tile_bytes);
       const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off + s * L.cost_bytes);
       float2 v[NREG], w[NREG];
-      lds_round<PL, 0>(v, bv);
+      lds_round<PL, 0, SW>(v, bv);
       if (P.init_lambda) {
         // lambda = f psi: the derivative of E = <psi|f|psi> with respect to psi^*
         const uint32_t tt = thr_tile<PL, 0>();
@@ -654,23 +699,23 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
           w[r] = f2(f * v[r].x, f * v[r].y);
         }
       } else {
-        lds_round<PL, 0>(w, bw);
+        lds_round<PL, 0, SW>(w, bw);
       }
       float a1 = 0.f, ag = 0.f, a2 = 0.f;
-      unrot_tan<EB>(v, w, P.s1.m[0], P.tau1, P.form1, P.w1[0], a1);
-      sts_round<PL, 0>(v, bv);
-      sts_round<PL, 0>(w, bw);
+      unrot_tan<EB>(v, w, P.s1.m[0], P.s1.lm[0], P.tau1, P.form1, P.w1[0], a1);
+      sts_round<PL, 0, SW>(v, bv);
+      sts_round<PL, 0, SW>(w, bw);
       cbar();
-      lds_round<PL, 1>(v, bv);
-      lds_round<PL, 1>(w, bw);
-      unrot_tan<EB>(v, w, P.s1.m[1], P.tau1, P.form1, P.w1[1], a1);
+      lds_round<PL, 1, SW>(v, bv);
+      lds_round<PL, 1, SW>(w, bw);
+      unrot_tan<EB>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
       if constexpr (NR == 3) {
-        sts_round<PL, 1>(v, bv);
-        sts_round<PL, 1>(w, bw);
+        sts_round<PL, 1, SW>(v, bv);
+        sts_round<PL, 1, SW>(w, bw);
         cbar();
-        lds_round<PL, 2>(v, bv);
-        lds_round<PL, 2>(w, bw);
-        unrot_tan<EB>(v, w, P.s1.m[2], P.tau1, P.form1, P.w1[2], a1);
+        lds_round<PL, 2, SW>(v, bv);
+        lds_round<PL, 2, SW>(w, bw);
+        unrot_tan<EB>(v, w, P.s1.m[2], P.s1.lm[2], P.tau1, P.form1, P.w1[2], a1);
       }
       if (P.has_phase) {
         // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
@@ -688,29 +733,29 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       }
       bool final0 = false;
       if (has2) {
-        unrot_tan<EB>(v, w, P.s2.m[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
+        unrot_tan<EB>(v, w, P.s2.m[NR - 1], P.s2.lm[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
         if constexpr (NR == 3) {
-          sts_round<PL, 2>(v, bv);
-          sts_round<PL, 2>(w, bw);
+          sts_round<PL, 2, SW>(v, bv);
+          sts_round<PL, 2, SW>(w, bw);
           cbar();
-          lds_round<PL, 1>(v, bv);
-          lds_round<PL, 1>(w, bw);
-          unrot_tan<EB>(v, w, P.s2.m[1], P.tau2, P.form2, P.w2[1], a2);
+          lds_round<PL, 1, SW>(v, bv);
+          lds_round<PL, 1, SW>(w, bw);
+          unrot_tan<EB>(v, w, P.s2.m[1], P.s2.lm[1], P.tau2, P.form2, P.w2[1], a2);
         }
-        sts_round<PL, 1>(v, bv);
-        sts_round<PL, 1>(w, bw);
+        sts_round<PL, 1, SW>(v, bv);
+        sts_round<PL, 1, SW>(w, bw);
         cbar();
-        lds_round<PL, 0>(v, bv);
-        lds_round<PL, 0>(w, bw);
-        unrot_tan<EB>(v, w, P.s2.m[0], P.tau2, P.form2, P.w2[0], a2);
+        lds_round<PL, 0, SW>(v, bv);
+        lds_round<PL, 0, SW>(w, bw);
+        unrot_tan<EB>(v, w, P.s2.m[0], P.s2.lm[0], P.tau2, P.form2, P.w2[0], a2);
         final0 = true;
       }
       if (final0) {
-        sts_round<PL, 0>(v, bv);
-        sts_round<PL, 0>(w, bw);
+        sts_round<PL, 0, SW>(v, bv);
+        sts_round<PL, 0, SW>(w, bw);
       } else {
-        sts_round<PL, NR - 1>(v, bv);
-        sts_round<PL, NR - 1>(w, bw);
+        sts_round<PL, NR - 1, SW>(v, bv);
+        sts_round<PL, NR - 1, SW>(w, bw);
       }
       fence_async_smem();
       if constexpr (NS == 2) {
@@ -770,27 +815,33 @@ EncodeFn encode_fn() {
 }  // namespace
 
 // 5-D tile view of a 2^n vector of `esz`-byte elements for tiles of 2^tb
-// elements: [16][2^(h-4)][256][2^(tb-12)][2^(n-h-(tb-4))]; one box = one tile.
-cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, int esz, bool swizzle) {
+// elements with 2^c contiguous ones:
+// [2^c][2^(h-c)][256][2^(tb-c-8)][2^(n-h-(tb-c))]; one box = one tile.
+cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, int c, int esz,
+                          int swizzle_bytes) {
   EncodeFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
-  const int hi = tb - 12;  // extra high-segment bits beyond 256 rows
-  cuuint64_t dims[5] = {16, 1ull << (h - 4), 256, 1ull << hi, 1ull << (n - h - (tb - 4))};
+  const int hi = tb - c - 8;  // extra high-segment bits beyond 256 rows
+  if (hi < 0 || h < c || n < h + tb - c) return cudaErrorInvalidValue;
+  cuuint64_t dims[5] = {1ull << c, 1ull << (h - c), 256, 1ull << hi, 1ull << (n - h - (tb - c))};
   const cuuint64_t e = (cuuint64_t)esz;
-  cuuint64_t strides[4] = {16 * e, (1ull << h) * e, (1ull << (h + 8)) * e, (1ull << (h + 8 + hi)) * e};
-  cuuint32_t box[5] = {16, 1, 256, (cuuint32_t)(1u << hi), 1};
+  cuuint64_t strides[4] = {(1ull << c) * e, (1ull << h) * e, (1ull << (h + 8)) * e,
+                           (1ull << (h + 8 + hi)) * e};
+  cuuint32_t box[5] = {(cuuint32_t)(1u << c), 1, 256, (cuuint32_t)(1u << hi), 1};
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   const CUtensorMapDataType dt = esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
-  const CUresult r = fn(map, dt, 5, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+  const CUtensorMapSwizzle sw = swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                      : CU_TENSOR_MAP_SWIZZLE_NONE;
+  const CUresult r = fn(map, dt, 5, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <class PL, int NS>
+template <class PL, int NS, int SW>
 static cudaError_t launch_fwd_tma_t(const TmaFwdParams &P, cudaStream_t s, int nsm) {
   const size_t smem = tma_smem_bytes(PL::TB, false, P.has_phase || P.reduce, NS);
-  auto kern = k_fwd_tma<PL, NS>;
+  auto kern = k_fwd_tma<PL, NS, SW>;
   static int nb = 0;
   if (nb == 0) {
     const size_t mx = tma_smem_bytes(PL::TB, false, true, NS);
@@ -806,10 +857,10 @@ static cudaError_t launch_fwd_tma_t(const TmaFwdParams &P, cudaStream_t s, int n
   return cudaGetLastError();
 }
 
-template <class PL, int NS>
+template <class PL, int NS, int SW>
 static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int nsm) {
   const size_t smem = tma_smem_bytes(PL::TB, true, P.has_phase || P.init_lambda, NS);
-  auto kern = k_bwd_tma<PL, NS>;
+  auto kern = k_bwd_tma<PL, NS, SW>;
   static int nb = 0;
   if (nb == 0) {
     const size_t mx = tma_smem_bytes(PL::TB, true, true, NS);
@@ -831,14 +882,16 @@ static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int n
 
 cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm) {
   constexpr int NS = QAOA_TMA_STAGES;
-  return high ? launch_fwd_tma_t<PlanTmaF13High, NS>(P, s, nsm)
-              : launch_fwd_tma_t<PlanTmaF13Low, NS>(P, s, nsm);
+  return high ? launch_fwd_tma_t<PlanTmaF13High, NS, 128>(P, s, nsm)
+              : launch_fwd_tma_t<PlanTmaF13Low, NS, 128>(P, s, nsm);
 }
 
 cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {
   constexpr int NS = QAOA_TMA_STAGES;
-  return high ? launch_bwd_tma_t<PlanTmaB12High, NS>(P, s, nsm)
-              : launch_bwd_tma_t<PlanTmaB12Low, NS>(P, s, nsm);
+  if (!high) return launch_bwd_tma_t<PlanTmaB12Low, NS, 128>(P, s, nsm);
+  // 8-amplitude (64-byte) segments: HIGH passes rotate 9 qubits
+  return P.c == 3 ? launch_bwd_tma_t<PlanTmaB12High, NS, 64>(P, s, nsm)
+                  : launch_bwd_tma_t<PlanTmaB12High, NS, 128>(P, s, nsm);
 }
 
 }  // namespace qaoa
