@@ -198,6 +198,32 @@ qaoa_status qaoa_simulate(int n, const void *d_costs, qaoa_cost_type ct,
                           size_t work_bytes, double *d_out,
                           qaoa_stream_t stream);
 
+/*
+ * qaoa_simulate without a workspace argument, for callers that cannot
+ * allocate device memory (the paper has no counterpart): for example a plugin
+ * whose host application owns every device allocation and forbids any outside
+ * its own pool, or a caller whose fixed device-memory budget is already fully
+ * committed.  The caller still provides d_costs, d_state and d_out exactly as
+ * for qaoa_simulate; the scratch (reduction partials, counters, error word)
+ * is a fixed 128.5 KiB device array inside the library, which every GPU that
+ * loads the library holds until the process exits.
+ *   - Maximum n = 23; a larger n returns QAOA_ERR_OUT_OF_MEMORY with a
+ *     message, before anything is enqueued.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and each call clears the parts that must
+ *     start at zero.  Calls that overlap on the GPU (different streams,
+ *     different host threads) race on it: order them on one stream.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * Arguments, results and errors otherwise as qaoa_simulate.
+ */
+qaoa_status qaoa_simulate_noalloc(int n, const void *d_costs, qaoa_cost_type ct,
+                                  const qaoa_cost_stats *stats, const double *gammas,
+                                  const double *betas, int p, void *d_state,
+                                  qaoa_state_type st, int init_plus, double *d_out,
+                                  qaoa_stream_t stream);
+
 /* ---------------------------------------------------- a5: reductions */
 
 /*

@@ -696,6 +696,10 @@ bool dyadic_scale(const double *w, size_t m, int *e_out) {
 
 }  // namespace
 
+namespace qaoa {
+void set_last_error(const char *msg) { fail(QAOA_OK, msg); }
+}  // namespace qaoa
+
 // =================================================================== C ABI
 
 extern "C" {

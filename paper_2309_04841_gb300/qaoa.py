@@ -69,6 +69,7 @@ def lib():
             "qaoa_overlap": ([I, P, I, P, I, P, P, Z, P, P], I),
             "qaoa_grad": ([I, P, I, P, P, P, I, P, P, I, P, Z, P, P], I),
             "qaoa_workspace_check": ([P, Z, P], I),
+            "qaoa_simulate_noalloc": ([I, P, I, P, P, P, I, P, I, I, P, P], I),
             "qaoa_profile_enable": ([I], I),
             "qaoa_profile_read": ([P, I, P, I], I),
         }
@@ -249,6 +250,25 @@ def simulate(costs, stats, gammas, betas, state=None, state_type=C64, init_plus=
                                1 if init_plus else 0, _ptr(work), work.numel(),
                                _ptr(out) if reduce else None, _stream()))
     return state, (out if reduce else None)
+
+
+def simulate_noalloc(costs, stats, gammas, betas, state=None, state_type=C64, init_plus=True,
+                     out=None):
+    """qaoa_simulate_noalloc: as simulate() with the library's built-in
+    scratch instead of a workspace (n <= 23).  Returns (state, out)."""
+    torch = _torch()
+    n = _n_of(costs)
+    g, b = _angles(gammas, betas)
+    if state is None:
+        state = torch.empty(1 << n, dtype=state_dtype(state_type), device="cuda")
+        init_plus = True
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device="cuda")
+    _check(lib().qaoa_simulate_noalloc(n, _ptr(costs), cost_type_of(costs), C.byref(stats),
+                                       _np_ptr(g), _np_ptr(b), len(g), _ptr(state),
+                                       state_type_of(state), 1 if init_plus else 0, _ptr(out),
+                                       _stream()))
+    return state, out
 
 
 def expectation(state, costs, work=None, out=None):
