@@ -267,6 +267,85 @@ qaoa_status qaoa_grad(int n, const void *d_costs, qaoa_cost_type ct,
                       void *d_lambda, qaoa_state_type st, void *d_work,
                       size_t work_bytes, double *d_out, qaoa_stream_t stream);
 
+/* ------------------------------------------------------ a7: serving loop */
+
+/*
+ * Continuous-batching request server (not in the paper).  Objective or
+ * objective + gradient requests of any n (2..32) and p arrive at any time
+ * (qaoa_server_submit returns at once).  A scheduler thread admits them as
+ * GPU slots and device memory free up and runs admitted work concurrently:
+ * requests with n <= 12 and p <= 128 are packed many per kernel launch (one
+ * CTA each, state on chip); larger ones run on their own CUDA streams, up to
+ * max_inflight units at a time.  All device memory comes from one
+ * caller-owned arena (d_arena, arena_bytes), sub-allocated by the server:
+ * a running request holds its state (8 B x 2^n, complex64), lambda (the same,
+ * gradient requests only), workspace and outputs; cost vectors are cached per
+ * (problem, n, problem_key) and evicted least recently used.  A request that
+ * cannot fit the arena even when it is empty is rejected (its ticket reports
+ * QAOA_ERR_REJECTED).  Results depend only on the request: the same
+ * request gives bit-identical results alone and in any mix.
+ */
+typedef struct qaoa_server qaoa_server;
+
+typedef enum { QAOA_PROBLEM_LABS = 0, QAOA_PROBLEM_MAXCUT = 1 } qaoa_problem;
+
+typedef struct {
+    int max_inflight;  /* GPU work units (streams) at once, 1..64           */
+    int max_queue;     /* pending requests accepted before QAOA_ERR_BUSY    */
+    int small_batch;   /* most n <= 12 requests packed into one launch      */
+} qaoa_server_config;
+
+typedef struct {
+    qaoa_problem problem;
+    int n, p;
+    const int32_t *edges;   /* MaxCut: host, 2m vertex indices (copied)      */
+    const double *weights;  /* MaxCut: host, m weights or NULL for 1 (copied) */
+    size_t m;               /* MaxCut edge count, <= 1536                     */
+    uint64_t problem_key;   /* equal (problem, n, key) => same cost vector    */
+    const double *gammas;   /* host, p angles (copied)                        */
+    const double *betas;    /* host, p angles (copied)                        */
+    int want_grad;          /* 0: E and O only; 1: also all 2p derivatives    */
+} qaoa_request;
+
+typedef struct {
+    qaoa_status status;     /* QAOA_OK, _REJECTED, _CANCELLED or an error   */
+    double energy, overlap; /* E and O of the final state                     */
+    double submit_s, admit_s, finish_s; /* host steady-clock seconds         */
+} qaoa_result;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, cancelled;
+    double p50_ms, p99_ms;  /* latency (finish - submit) of completed ones    */
+    double evals_per_s;     /* completed / (last finish - first submit)       */
+    size_t arena_bytes, arena_peak_bytes, cached_cost_vectors;
+} qaoa_server_stats_t;
+
+/* Creates the server and its scheduler thread on the current device.  The
+ * arena (device, 256-byte aligned, >= 1 MiB) stays owned by the caller and
+ * must outlive the server. */
+qaoa_status qaoa_server_create(const qaoa_server_config *cfg, void *d_arena, size_t arena_bytes,
+                               qaoa_server **out);
+
+/* Queues a request (all inputs copied) and returns its ticket; never blocks
+ * on the GPU.  QAOA_ERR_BUSY when max_queue requests are pending. */
+qaoa_status qaoa_server_submit(qaoa_server *srv, const qaoa_request *req, uint64_t *ticket);
+
+/* Waits up to timeout_ms (< 0: forever) for the ticket, fills *out and, for
+ * gradient requests, h_dgamma / h_dbeta (host, p each, may be NULL), then
+ * forgets the ticket.  QAOA_ERR_TIMEOUT leaves the ticket valid. */
+qaoa_status qaoa_server_wait(qaoa_server *srv, uint64_t ticket, qaoa_result *out,
+                             double *h_dgamma, double *h_dbeta, int timeout_ms);
+
+/* Cancels a pending request; a running one finishes on the GPU and reports
+ * QAOA_ERR_CANCELLED. */
+qaoa_status qaoa_server_cancel(qaoa_server *srv, uint64_t ticket);
+
+qaoa_status qaoa_server_stats(qaoa_server *srv, qaoa_server_stats_t *out);
+
+/* Stops the scheduler, waits for running work, releases streams and pinned
+ * host buffers (the arena is the caller's). */
+qaoa_status qaoa_server_destroy(qaoa_server *srv);
+
 /* ------------------------------------------------------------ profiling */
 
 /* Per-kernel-kind launch statistics (not in the paper; measurement aid). */

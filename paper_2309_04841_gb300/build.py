@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqaoa.so")
 SOURCES = ["api.cu", "pass_kernels.cu", "small_kernels.cu", "cost_kernels.cu", "profile.cu",
-           "tma_kernels.cu", "noalloc.cu"]
+           "tma_kernels.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

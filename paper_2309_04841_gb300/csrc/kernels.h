@@ -115,6 +115,8 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
 cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm);
 cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm);
 
+cudaError_t launch_small_batch(const SmallJob<float> *d_jobs, int count, int max_n, cudaStream_t s);
+cudaError_t launch_small_batch(const SmallJob<double> *d_jobs, int count, int max_n, cudaStream_t s);
 cudaError_t launch_small(const SmallParams<float> &P, cudaStream_t s);
 cudaError_t launch_small(const SmallParams<double> &P, cudaStream_t s);
 

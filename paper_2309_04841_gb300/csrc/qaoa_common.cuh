@@ -183,6 +183,24 @@ struct SmallLayer {
 };
 
 constexpr int kSmallMaxN = 12;
+
+// One request for the on-chip kernels (a launch of k_small runs one, a launch
+// of k_small_batch runs one per CTA from a device array of these).
+template <typename Real>
+struct SmallJob {
+  using C2 = typename C2T<Real>::type;
+  C2 *psi, *lam;
+  const void *cost;
+  int cost_kind;
+  int n, nl;        // qubits; layers in this launch
+  int mode;         // 0 forward, 1 forward + adjoint, 2 adjoint only
+  int init_plus, init_lambda, reduce;
+  Real amp;
+  double fmin_d;
+  double *out;              // [E, O]
+  double *out_dg, *out_db;  // per-layer gradient outputs
+  const SmallLayer<Real> *L;
+};
 constexpr int kSmallMaxLayers = 128;
 
 template <typename Real>

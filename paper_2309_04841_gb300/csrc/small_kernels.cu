@@ -93,7 +93,7 @@ __device__ __forceinline__ void bsum(double (&a)[K], double *red) {
 // mode 2: adjoint sweep over layers [0, nl) in reverse, continuing from the
 //         psi / lambda stored by a previous launch (or lambda = f psi)
 template <typename Real>
-__global__ void __launch_bounds__(512) k_small(const __grid_constant__ SmallParams<Real> P) {
+__device__ __forceinline__ void small_run(const SmallJob<Real> &P) {
   using C2 = typename C2T<Real>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = P.n, N = 1 << n, H = N >> 1;
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(512) k_small(const __grid_constant__ SmallPara
 
   if (P.mode == 0 || P.mode == 1) {
     for (int li = 0; li < P.nl; ++li) {
-      const SmallLayer<Real> &L = P.L[li];
+      const SmallLayer<Real> L = P.L[li];
       for (int x = tid; x < N; x += nt) s[x] = cm(s[x], small_phase(L, P.cost, P.cost_kind, x));
       __syncthreads();
       for (int q = 0; q < n; ++q) {
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(512) k_small(const __grid_constant__ SmallPara
     }
     __syncthreads();
     for (int li = P.nl - 1; li >= 0; --li) {
-      const SmallLayer<Real> &L = P.L[li];
+      const SmallLayer<Real> L = P.L[li];
       double gb[1] = {0.0};
       const Real c = L.cb, sn = -L.sb;
       for (int q = 0; q < n; ++q) {
@@ -187,6 +187,35 @@ __global__ void __launch_bounds__(512) k_small(const __grid_constant__ SmallPara
 }
 
 template <typename Real>
+__global__ void __launch_bounds__(512) k_small(const __grid_constant__ SmallParams<Real> P) {
+  SmallJob<Real> J;
+  J.psi = P.psi;
+  J.lam = P.lam;
+  J.cost = P.cost;
+  J.cost_kind = P.cost_kind;
+  J.n = P.n;
+  J.nl = P.nl;
+  J.mode = P.mode;
+  J.init_plus = P.init_plus;
+  J.init_lambda = P.init_lambda;
+  J.reduce = P.reduce;
+  J.amp = P.amp;
+  J.fmin_d = P.fmin_d;
+  J.out = P.out;
+  J.out_dg = P.out_dg;
+  J.out_db = P.out_db;
+  J.L = P.L;
+  small_run<Real>(J);
+}
+
+// Many independent requests in one launch: CTA b runs jobs[b] (serving).
+template <typename Real>
+__global__ void __launch_bounds__(512) k_small_batch(const SmallJob<Real> *jobs) {
+  const SmallJob<Real> J = jobs[blockIdx.x];
+  small_run<Real>(J);
+}
+
+template <typename Real>
 static cudaError_t launch_small_t(const SmallParams<Real> &P, cudaStream_t st) {
   using C2 = typename C2T<Real>::type;
   const size_t smem = (size_t)2 * ((size_t)1 << P.n) * sizeof(C2) + 16 * 2 * sizeof(double);
@@ -205,5 +234,31 @@ static cudaError_t launch_small_t(const SmallParams<Real> &P, cudaStream_t st) {
 
 cudaError_t launch_small(const SmallParams<float> &P, cudaStream_t s) { return launch_small_t(P, s); }
 cudaError_t launch_small(const SmallParams<double> &P, cudaStream_t s) { return launch_small_t(P, s); }
+
+template <typename Real>
+static cudaError_t launch_small_batch_t(const SmallJob<Real> *d_jobs, int count, int max_n,
+                                       cudaStream_t st) {
+  using C2 = typename C2T<Real>::type;
+  static bool init = false;
+  if (!init) {
+    cudaError_t e = cudaFuncSetAttribute(k_small_batch<Real>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * (1 << kSmallMaxN) * sizeof(C2) + 256));
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  const size_t smem = (size_t)2 * ((size_t)1 << max_n) * sizeof(C2) + 16 * 2 * sizeof(double);
+  int nt = (1 << max_n) / 2;
+  nt = nt < 32 ? 32 : (nt > 512 ? 512 : nt);
+  k_small_batch<Real><<<count, nt, smem, st>>>(d_jobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_batch(const SmallJob<float> *d_jobs, int count, int max_n, cudaStream_t s) {
+  return launch_small_batch_t(d_jobs, count, max_n, s);
+}
+cudaError_t launch_small_batch(const SmallJob<double> *d_jobs, int count, int max_n, cudaStream_t s) {
+  return launch_small_batch_t(d_jobs, count, max_n, s);
+}
 
 }  // namespace qaoa

@@ -167,9 +167,10 @@ __device__ __forceinline__ void rot_lanes(float2 (&v)[N], uint32_t lm, float tau
 // Adjoint: reduced-form un-rotation of psi (v) and lambda (w), adding the raw
 // Im <lambda| X_q |psi> of each pair first; the round's sum is weighted by wr
 // (the squared scale the stored vectors owe at this point).
-template <int EB>
+template <int EB, bool LANES>
 __device__ __forceinline__ void unrot_tan(float2 (&v)[1 << EB], float2 (&w)[1 << EB], uint32_t m,
                                           uint32_t lm, float tau, int form, float wr, float &acc) {
+  if constexpr (!LANES) lm = 0u;
   if ((m | lm) == 0u) return;
   float racc = 0.f;
 #pragma unroll
@@ -182,6 +183,7 @@ __device__ __forceinline__ void unrot_tan(float2 (&v)[1 << EB], float2 (&w)[1 <<
           racc += la.x * pb.y - la.y * pb.x + lb.x * pa.y - lb.y * pa.x;
         }
     }
+  if constexpr (LANES) {
 #pragma unroll
   for (int b = 0; b < 5; ++b)
     if ((lm >> b) & 1u) {
@@ -194,11 +196,14 @@ __device__ __forceinline__ void unrot_tan(float2 (&v)[1 << EB], float2 (&w)[1 <<
         racc += w[r].x * py - w[r].y * px;
       }
     }
+  }
   acc = fmaf(racc, wr, acc);
   rot_tan<EB>(v, m, tau, form);
   rot_tan<EB>(w, m, tau, form);
-  rot_lanes<(1 << EB)>(v, lm, tau, form);
-  rot_lanes<(1 << EB)>(w, lm, tau, form);
+  if constexpr (LANES) {
+    rot_lanes<(1 << EB)>(v, lm, tau, form);
+    rot_lanes<(1 << EB)>(w, lm, tau, form);
+  }
 }
 
 __device__ __forceinline__ uint32_t pdep_d(uint32_t v, uint32_t mask) {
@@ -507,27 +512,27 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       bool final0;
       if (has1) {
         rot_tan<EB>(v, P.s1.m[0], P.tau1, P.form1);
-        rot_lanes<NREG>(v, P.s1.lm[0], P.tau1, P.form1);
+        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s1.lm[0], P.tau1, P.form1);
         xp<PL, 0, 1, SW>(v, buf);
         rot_tan<EB>(v, P.s1.m[1], P.tau1, P.form1);
-        rot_lanes<NREG>(v, P.s1.lm[1], P.tau1, P.form1);
+        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s1.lm[1], P.tau1, P.form1);
         if constexpr (NR == 3) {
           xp<PL, 1, 2, SW>(v, buf);
           rot_tan<EB>(v, P.s1.m[2], P.tau1, P.form1);
-        rot_lanes<NREG>(v, P.s1.lm[2], P.tau1, P.form1);
+        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s1.lm[2], P.tau1, P.form1);
         }
         if (P.has_phase) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
         if (has2) {
           rot_tan<EB>(v, P.s2.m[NR - 1], P.tau2, P.form2);
-        rot_lanes<NREG>(v, P.s2.lm[NR - 1], P.tau2, P.form2);
+        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[NR - 1], P.tau2, P.form2);
           if constexpr (NR == 3) {
             xp<PL, 2, 1, SW>(v, buf);
             rot_tan<EB>(v, P.s2.m[1], P.tau2, P.form2);
-        rot_lanes<NREG>(v, P.s2.lm[1], P.tau2, P.form2);
+        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[1], P.tau2, P.form2);
           }
           xp<PL, 1, 0, SW>(v, buf);
           rot_tan<EB>(v, P.s2.m[0], P.tau2, P.form2);
-        rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
+        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
           final0 = true;
         } else {
           final0 = false;
@@ -535,14 +540,14 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       } else {
         if (P.has_phase) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
         rot_tan<EB>(v, P.s2.m[0], P.tau2, P.form2);
-        rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
+        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
         xp<PL, 0, 1, SW>(v, buf);
         rot_tan<EB>(v, P.s2.m[1], P.tau2, P.form2);
-        rot_lanes<NREG>(v, P.s2.lm[1], P.tau2, P.form2);
+        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[1], P.tau2, P.form2);
         if constexpr (NR == 3) {
           xp<PL, 1, 2, SW>(v, buf);
           rot_tan<EB>(v, P.s2.m[2], P.tau2, P.form2);
-        rot_lanes<NREG>(v, P.s2.lm[2], P.tau2, P.form2);
+        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[2], P.tau2, P.form2);
         }
         final0 = false;
       }
@@ -702,20 +707,20 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
         lds_round<PL, 0, SW>(w, bw);
       }
       float a1 = 0.f, ag = 0.f, a2 = 0.f;
-      unrot_tan<EB>(v, w, P.s1.m[0], P.s1.lm[0], P.tau1, P.form1, P.w1[0], a1);
+      unrot_tan<EB, SW == 64>(v, w, P.s1.m[0], P.s1.lm[0], P.tau1, P.form1, P.w1[0], a1);
       sts_round<PL, 0, SW>(v, bv);
       sts_round<PL, 0, SW>(w, bw);
       cbar();
       lds_round<PL, 1, SW>(v, bv);
       lds_round<PL, 1, SW>(w, bw);
-      unrot_tan<EB>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
+      unrot_tan<EB, SW == 64>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
       if constexpr (NR == 3) {
         sts_round<PL, 1, SW>(v, bv);
         sts_round<PL, 1, SW>(w, bw);
         cbar();
         lds_round<PL, 2, SW>(v, bv);
         lds_round<PL, 2, SW>(w, bw);
-        unrot_tan<EB>(v, w, P.s1.m[2], P.s1.lm[2], P.tau1, P.form1, P.w1[2], a1);
+        unrot_tan<EB, SW == 64>(v, w, P.s1.m[2], P.s1.lm[2], P.tau1, P.form1, P.w1[2], a1);
       }
       if (P.has_phase) {
         // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
@@ -733,21 +738,21 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       }
       bool final0 = false;
       if (has2) {
-        unrot_tan<EB>(v, w, P.s2.m[NR - 1], P.s2.lm[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
+        unrot_tan<EB, SW == 64>(v, w, P.s2.m[NR - 1], P.s2.lm[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
         if constexpr (NR == 3) {
           sts_round<PL, 2, SW>(v, bv);
           sts_round<PL, 2, SW>(w, bw);
           cbar();
           lds_round<PL, 1, SW>(v, bv);
           lds_round<PL, 1, SW>(w, bw);
-          unrot_tan<EB>(v, w, P.s2.m[1], P.s2.lm[1], P.tau2, P.form2, P.w2[1], a2);
+          unrot_tan<EB, SW == 64>(v, w, P.s2.m[1], P.s2.lm[1], P.tau2, P.form2, P.w2[1], a2);
         }
         sts_round<PL, 1, SW>(v, bv);
         sts_round<PL, 1, SW>(w, bw);
         cbar();
         lds_round<PL, 0, SW>(v, bv);
         lds_round<PL, 0, SW>(w, bw);
-        unrot_tan<EB>(v, w, P.s2.m[0], P.s2.lm[0], P.tau2, P.form2, P.w2[0], a2);
+        unrot_tan<EB, SW == 64>(v, w, P.s2.m[0], P.s2.lm[0], P.tau2, P.form2, P.w2[0], a2);
         final0 = true;
       }
       if (final0) {

@@ -34,6 +34,31 @@ class ProfEntry(C.Structure):
                 ("bytes", C.c_double)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("max_inflight", C.c_int), ("max_queue", C.c_int), ("small_batch", C.c_int)]
+
+
+class Request(C.Structure):
+    _fields_ = [("problem", C.c_int), ("n", C.c_int), ("p", C.c_int), ("edges", C.c_void_p),
+                ("weights", C.c_void_p), ("m", C.c_size_t), ("problem_key", C.c_uint64),
+                ("gammas", C.c_void_p), ("betas", C.c_void_p), ("want_grad", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("energy", C.c_double), ("overlap", C.c_double),
+                ("submit_s", C.c_double), ("admit_s", C.c_double), ("finish_s", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("rejected", C.c_uint64),
+                ("cancelled", C.c_uint64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("evals_per_s", C.c_double), ("arena_bytes", C.c_size_t),
+                ("arena_peak_bytes", C.c_size_t), ("cached_cost_vectors", C.c_size_t)]
+
+
+PROBLEM_LABS, PROBLEM_MAXCUT = 0, 1
+
+
 class CostStats(C.Structure):
     _fields_ = [("f_min", C.c_double), ("f_max", C.c_double), ("n_min", C.c_uint64)]
 
@@ -70,6 +95,12 @@ def lib():
             "qaoa_grad": ([I, P, I, P, P, P, I, P, P, I, P, Z, P, P], I),
             "qaoa_workspace_check": ([P, Z, P], I),
             "qaoa_simulate_noalloc": ([I, P, I, P, P, P, I, P, I, I, P, P], I),
+            "qaoa_server_create": ([P, P, Z, P], I),
+            "qaoa_server_submit": ([P, P, P], I),
+            "qaoa_server_wait": ([P, C.c_uint64, P, P, P, I], I),
+            "qaoa_server_cancel": ([P, C.c_uint64], I),
+            "qaoa_server_stats": ([P, P], I),
+            "qaoa_server_destroy": ([P], I),
             "qaoa_profile_enable": ([I], I),
             "qaoa_profile_read": ([P, I, P, I], I),
         }
@@ -362,3 +393,57 @@ def profile_read(reset=True):
     _check(lib().qaoa_profile_read(buf, 64, C.byref(cnt), 1 if reset else 0))
     return {buf[i].name.decode(): {"launches": int(buf[i].launches), "ms": float(buf[i].ms),
                                    "bytes": float(buf[i].bytes)} for i in range(min(cnt.value, 64))}
+
+
+# ---------------------------------------------------------------- serving
+
+class Server:
+    """qaoa_server_*: continuous-batching objective / gradient server over a
+    device arena (a torch uint8 tensor owned by this object)."""
+
+    def __init__(self, arena_bytes, max_inflight=8, max_queue=1 << 20, small_batch=256):
+        torch = _torch()
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
+        cfg = ServerConfig(max_inflight, max_queue, small_batch)
+        self._h = C.c_void_p()
+        _check(lib().qaoa_server_create(C.byref(cfg), _ptr(self.arena), self.arena.numel(),
+                                        C.byref(self._h)))
+
+    def submit(self, problem, n, gammas, betas, edges=None, weights=None, key=0, want_grad=True):
+        g, b = _angles(gammas, betas)
+        e = None if edges is None else np.ascontiguousarray(np.asarray(edges, np.int32).reshape(-1, 2))
+        w = None if weights is None else np.ascontiguousarray(np.asarray(weights, np.float64))
+        req = Request(problem, n, len(g), None if e is None else _np_ptr(e).value,
+                      None if w is None else _np_ptr(w).value, 0 if e is None else len(e), key,
+                      _np_ptr(g).value, _np_ptr(b).value, 1 if want_grad else 0)
+        t = C.c_uint64(0)
+        _check(lib().qaoa_server_submit(self._h, C.byref(req), C.byref(t)))  # inputs are copied
+        return t.value
+
+    def wait(self, ticket, p, timeout_ms=-1):
+        r = Result()
+        dg = np.zeros(p)
+        db = np.zeros(p)
+        _check(lib().qaoa_server_wait(self._h, ticket, C.byref(r), _np_ptr(dg), _np_ptr(db),
+                                      int(timeout_ms)))
+        return {"status": r.status, "energy": r.energy, "overlap": r.overlap, "dgamma": dg,
+                "dbeta": db, "submit_s": r.submit_s, "admit_s": r.admit_s, "finish_s": r.finish_s}
+
+    def cancel(self, ticket):
+        _check(lib().qaoa_server_cancel(self._h, ticket))
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().qaoa_server_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().qaoa_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

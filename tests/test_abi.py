@@ -135,3 +135,12 @@ def test_precompute_validation_without_gpu(L):
     e = np.array([[0, 0]], dtype=np.int32)
     st = L.qaoa_maxcut_costs(4, Q._np_ptr(e), None, 1, Q.COST_I32, C.c_void_p(16), None)
     assert st == 1  # self loop
+
+
+def test_server_validation_without_gpu(L):
+    cfg = Q.ServerConfig(0, 10, 10)  # max_inflight must be >= 1
+    h = C.c_void_p()
+    assert L.qaoa_server_create(C.byref(cfg), C.c_void_p(256), 1 << 30, C.byref(h)) == 1
+    cfg = Q.ServerConfig(4, 10, 10)
+    assert L.qaoa_server_create(C.byref(cfg), C.c_void_p(100), 1 << 30, C.byref(h)) == 1  # alignment
+    assert L.qaoa_server_submit(None, None, None) == 1

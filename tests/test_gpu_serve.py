@@ -1,0 +1,118 @@
+"""Serving loop (continuous batching): every result is the same alone and in
+a mix (bit for bit, the kernels are deterministic and a request's arithmetic
+depends only on its inputs), agrees with the oracle and with the plain
+qaoa_grad path, and admission / cancel / timeout behave as documented."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_04841_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_2309_04841_gb300 import qaoa
+    qaoa.lib()
+    return qaoa
+
+
+def make_requests():
+    reqs = []
+    k = 0
+    for n in (5, 8, 11, 12, 13, 15, 18, 21):
+        for problem in (0, 1):
+            for want_grad in (True, False):
+                k += 1
+                p = 1 + (k % 5)
+                g = I.angles(p, 100 + k, 0, 0.3)
+                b = I.angles(p, 200 + k)
+                if problem == 1:
+                    m = n + (n % 2)
+                    edges, w = I.maxcut_3reg(m, graph_seed=n, weighted=bool(k % 2), weight_seed=k)
+                    nn = m
+                else:
+                    edges = w = None
+                    nn = n
+                reqs.append(dict(problem=problem, n=nn, gammas=g, betas=b, edges=edges,
+                                 weights=w, key=n * 10 + (k % 2), want_grad=want_grad))
+    return reqs
+
+
+def run(server, reqs, together):
+    out = []
+    if together:
+        ts = [server.submit(**r) for r in reqs]
+        out = [server.wait(t, len(r["gammas"])) for t, r in zip(ts, reqs)]
+    else:
+        for r in reqs:
+            out.append(server.wait(server.submit(**r), len(r["gammas"])))
+    return out
+
+
+def test_alone_vs_mix_bit_identical(Q):
+    reqs = make_requests()
+    srv = Q.Server(4 << 30, max_inflight=6)
+    alone = run(srv, reqs, together=False)
+    mixed = run(srv, reqs, together=True)
+    srv.close()
+    for a, m, r in zip(alone, mixed, reqs):
+        assert a["status"] == 0 and m["status"] == 0, (a["status"], m["status"])
+        assert a["energy"] == m["energy"] and a["overlap"] == m["overlap"], r["n"]
+        if r["want_grad"]:
+            np.testing.assert_array_equal(a["dgamma"], m["dgamma"])
+            np.testing.assert_array_equal(a["dbeta"], m["dbeta"])
+
+
+def test_results_match_oracle_and_plain_path(Q):
+    reqs = [r for r in make_requests() if r["want_grad"]]
+    srv = Q.Server(4 << 30, max_inflight=4)
+    res = run(srv, reqs, together=True)
+    srv.close()
+    for r, got in zip(reqs, res):
+        n = r["n"]
+        if r["problem"] == 0:
+            f = oracle.labs_costs(n).astype(float)
+            fd = Q.labs_costs(n)
+        else:
+            f = oracle.maxcut_costs(n, r["edges"], r["weights"])
+            integer = np.all(np.asarray(r["weights"]) == np.rint(r["weights"]))
+            if not integer:
+                f = oracle.to_f32_rne(f).astype(float)
+            fd = Q.maxcut_costs(n, r["edges"], r["weights"],
+                                cost_type=Q.COST_I32 if integer else Q.COST_F32)
+        E, dg, db = oracle.grad(n, f, r["gammas"], r["betas"])
+        assert abs(got["energy"] - E) <= 1e-5 * abs(E)
+        ref = np.concatenate([dg, db])
+        assert np.linalg.norm(np.concatenate([got["dgamma"], got["dbeta"]]) - ref) <= 1e-4 * np.linalg.norm(ref)
+        if n > 12:
+            st = Q.cost_stats_compute(fd)
+            plain = Q.grad(fd, st, r["gammas"], r["betas"]).cpu().numpy()
+            assert abs(plain[0] - got["energy"]) <= 1e-6 * abs(E)
+
+
+def test_rejects_what_can_never_fit(Q):
+    srv = Q.Server(64 << 20, max_inflight=2)
+    t = srv.submit(0, 24, [0.1], [0.2], want_grad=True)  # 2 x 128 MiB state
+    assert srv.wait(t, 1)["status"] == 6  # QAOA_ERR_REJECTED
+    ok = srv.submit(0, 10, [0.1], [0.2])
+    assert srv.wait(ok, 1)["status"] == 0
+    assert srv.stats()["rejected"] == 1
+    srv.close()
+
+
+def test_cancel_and_timeout(Q):
+    srv = Q.Server(2 << 30, max_inflight=1)
+    g, b = I.angles(40, 1, 0, 0.05), I.angles(40, 2)
+    big = srv.submit(0, 26, g, b, want_grad=True)
+    queued = srv.submit(0, 26, g, b, want_grad=True, key=1)
+    srv.cancel(queued)
+    with pytest.raises(Q.QAOAError) as ei:
+        srv.wait(big, 40, timeout_ms=0)
+    assert ei.value.status == 5  # timeout: the ticket stays valid
+    assert srv.wait(big, 40)["status"] == 0
+    assert srv.wait(queued, 40)["status"] == 7  # cancelled
+    st = srv.stats()
+    assert st["completed"] == 1 and st["cancelled"] == 1 and st["p99_ms"] >= st["p50_ms"] > 0
+    srv.close()
