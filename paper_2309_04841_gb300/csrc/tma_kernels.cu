@@ -413,12 +413,17 @@ template <int NS> struct TmaCfg {
   static constexpr int MINB = NS == 1 ? 2 : 1;
 };
 
-template <class PL, int NS, int SW>
+// Pass kinds, fixed at compile time so each instantiation carries only its
+// own path: forward  K = kH1 | kPH | kH2 | kRED,  adjoint  K = kPH | kH2 | kINIT.
+constexpr int kH1 = 1, kPH = 2, kH2 = 4, kRED = 8, kINIT = 8;
+
+template <class PL, int NS, int SW, int K>
 __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     k_fwd_tma(const __grid_constant__ TmaFwdParams P) {
   constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, NT = TmaCfg<NS>::NT;
+  constexpr bool H1 = (K & kH1) != 0, PH = (K & kPH) != 0, H2 = (K & kH2) != 0, RED = (K & kRED) != 0;
   extern __shared__ unsigned char smem_raw[];
-  const bool need_cost = P.has_phase || P.reduce;
+  constexpr bool need_cost = PH || RED;
   unsigned char *base = aligned_base(smem_raw);
   const Lay L = layout(1u << PL::TB, false, need_cost, NS);
   float2 *tlo = reinterpret_cast<float2 *>(base + L.tab_off), *thi = tlo + 256;
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
   const int midbits = P.h - P.c;
   __shared__ int s_abort;
 
-  if (P.has_phase && P.ph.mode == 0)
+  if (PH && P.ph.mode == 0)
     for (int i = tid; i < 256; i += NT) {
       tlo[i] = P.ph.tab_lo[i];
       thi[i] = P.ph.tab_hi[i];
@@ -486,8 +491,6 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     }
   } else {
     // ---------------- compute warps
-    const bool has1 = (P.s1.m[0] | P.s1.m[1] | P.s1.m[2] | P.s1.lm[0] | P.s1.lm[1] | P.s1.lm[2]) != 0;
-    const bool has2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2] | P.s2.lm[0] | P.s2.lm[1] | P.s2.lm[2]) != 0;
     for (int i = 0;; ++i) {
       const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
       if (T >= P.ntiles) break;
@@ -509,8 +512,8 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       } else {
         lds_round<PL, 0, SW>(v, buf);
       }
-      bool final0;
-      if (has1) {
+      constexpr bool final0 = H1 && H2;  // s2 walks back down to round 0
+      if constexpr (H1) {
         rot_tan<EB>(v, P.s1.m[0], P.tau1, P.form1);
         if constexpr (SW == 64) rot_lanes<NREG>(v, P.s1.lm[0], P.tau1, P.form1);
         xp<PL, 0, 1, SW>(v, buf);
@@ -521,8 +524,8 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
           rot_tan<EB>(v, P.s1.m[2], P.tau1, P.form1);
         if constexpr (SW == 64) rot_lanes<NREG>(v, P.s1.lm[2], P.tau1, P.form1);
         }
-        if (P.has_phase) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
-        if (has2) {
+        if constexpr (PH) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
+        if constexpr (H2) {
           rot_tan<EB>(v, P.s2.m[NR - 1], P.tau2, P.form2);
         if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[NR - 1], P.tau2, P.form2);
           if constexpr (NR == 3) {
@@ -532,13 +535,10 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
           }
           xp<PL, 1, 0, SW>(v, buf);
           rot_tan<EB>(v, P.s2.m[0], P.tau2, P.form2);
-        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
-          final0 = true;
-        } else {
-          final0 = false;
+          if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
         }
       } else {
-        if (P.has_phase) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
+        if constexpr (PH) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
         rot_tan<EB>(v, P.s2.m[0], P.tau2, P.form2);
         if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
         xp<PL, 0, 1, SW>(v, buf);
@@ -547,20 +547,19 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
         if constexpr (NR == 3) {
           xp<PL, 1, 2, SW>(v, buf);
           rot_tan<EB>(v, P.s2.m[2], P.tau2, P.form2);
-        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[2], P.tau2, P.form2);
+          if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[2], P.tau2, P.form2);
         }
-        final0 = false;
       }
       if (P.end_scale) {
 #pragma unroll
         for (int r = 0; r < NREG; ++r) v[r] = cmulf(v[r], P.scl_end);
       }
       float e = 0.f, o = 0.f;
-      if (final0) {
-        if (P.reduce) eo_round<PL, 0>(v, cb, P.cost_kind, P.fmin_d, e, o);
+      if constexpr (final0) {
+        if constexpr (RED) eo_round<PL, 0>(v, cb, P.cost_kind, P.fmin_d, e, o);
         sts_round<PL, 0, SW>(v, buf);
       } else {
-        if (P.reduce) eo_round<PL, NR - 1>(v, cb, P.cost_kind, P.fmin_d, e, o);
+        if constexpr (RED) eo_round<PL, NR - 1>(v, cb, P.cost_kind, P.fmin_d, e, o);
         sts_round<PL, NR - 1, SW>(v, buf);
       }
       fence_async_smem();
@@ -580,7 +579,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
           }
         }
       }
-      if (P.reduce) {
+      if constexpr (RED) {
         double a[2] = {(double)e, (double)o};
         csum<2>(a, red);
         if (tid == 0) {
@@ -591,7 +590,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     }
     if (NS == 1 && tid == 0) bulk_wait0();
   }
-  if (P.reduce) {
+  if constexpr (RED) {
     double *out = P.out;
     final_reduce<2>(P.partials, P.ntiles, P.counter, red, [out](double(&a)[2]) {
       out[0] = a[0];
@@ -602,12 +601,13 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
 
 // ------------------------------------------------------------- adjoint
 
-template <class PL, int NS, int SW>
+template <class PL, int NS, int SW, int K>
 __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
   constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, NT = TmaCfg<NS>::NT;
+  constexpr bool PH = (K & kPH) != 0, H2 = (K & kH2) != 0, INIT = (K & kINIT) != 0;
   extern __shared__ unsigned char smem_raw[];
-  const bool need_cost = P.has_phase || P.init_lambda;
+  constexpr bool need_cost = PH || INIT;
   unsigned char *base = aligned_base(smem_raw);
   const Lay L = layout(1u << PL::TB, true, need_cost, NS);
   float2 *tlo = reinterpret_cast<float2 *>(base + L.tab_off), *thi = tlo + 256;
@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
   const int midbits = P.h - P.c;
   __shared__ int s_abort;
 
-  if (P.has_phase && P.ph.mode == 0)
+  if (PH && P.ph.mode == 0)
     for (int i = tid; i < 256; i += NT) {
       tlo[i] = P.ph.tab_lo[i];
       thi[i] = P.ph.tab_hi[i];
@@ -639,10 +639,10 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
   auto issue = [&](uint64_t T, int s) {
     int c1, c4;
     coords(T, c1, c4);
-    mbar_expect_tx(&full[s], L.tile_bytes + (P.init_lambda ? 0u : L.tile_bytes) +
+    mbar_expect_tx(&full[s], L.tile_bytes + (INIT ? 0u : L.tile_bytes) +
                                  (need_cost ? L.cost_bytes : 0u));
     tma_load(base + s * L.tile_bytes, &P.map_psi, c1, c4, &full[s]);
-    if (!P.init_lambda) tma_load(base + L.lam_off + s * L.tile_bytes, &P.map_lam, c1, c4, &full[s]);
+    if (!INIT) tma_load(base + L.lam_off + s * L.tile_bytes, &P.map_lam, c1, c4, &full[s]);
     if (need_cost) tma_load(base + L.cost_off + s * L.cost_bytes, &P.map_cost, c1, c4, &full[s]);
   };
   auto store = [&](uint64_t T, int s) {
@@ -679,7 +679,6 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       bulk_wait0();
     }
   } else {
-    const bool has2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2] | P.s2.lm[0] | P.s2.lm[1] | P.s2.lm[2]) != 0;
     for (int i = 0;; ++i) {
       const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
       if (T >= P.ntiles) break;
@@ -695,7 +694,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off + s * L.cost_bytes);
       float2 v[NREG], w[NREG];
       lds_round<PL, 0, SW>(v, bv);
-      if (P.init_lambda) {
+      if constexpr (INIT) {
         // lambda = f psi: the derivative of E = <psi|f|psi> with respect to psi^*
         const uint32_t tt = thr_tile<PL, 0>();
 #pragma unroll
@@ -722,7 +721,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
         lds_round<PL, 2, SW>(w, bw);
         unrot_tan<EB, SW == 64>(v, w, P.s1.m[2], P.s1.lm[2], P.tau1, P.form1, P.w1[2], a1);
       }
-      if (P.has_phase) {
+      if constexpr (PH) {
         // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
         const uint32_t tt = thr_tile<PL, NR - 1>();
 #pragma unroll
@@ -736,8 +735,8 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
           w[r] = cmulf(w[r], ph);
         }
       }
-      bool final0 = false;
-      if (has2) {
+      constexpr bool final0 = H2;
+      if constexpr (H2) {
         unrot_tan<EB, SW == 64>(v, w, P.s2.m[NR - 1], P.s2.lm[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
         if constexpr (NR == 3) {
           sts_round<PL, 2, SW>(v, bv);
@@ -753,9 +752,8 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
         lds_round<PL, 0, SW>(v, bv);
         lds_round<PL, 0, SW>(w, bw);
         unrot_tan<EB, SW == 64>(v, w, P.s2.m[0], P.s2.lm[0], P.tau2, P.form2, P.w2[0], a2);
-        final0 = true;
       }
-      if (final0) {
+      if constexpr (final0) {
         sts_round<PL, 0, SW>(v, bv);
         sts_round<PL, 0, SW>(w, bw);
       } else {
@@ -843,10 +841,10 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <class PL, int NS, int SW>
+template <class PL, int NS, int SW, int K>
 static cudaError_t launch_fwd_tma_t(const TmaFwdParams &P, cudaStream_t s, int nsm) {
-  const size_t smem = tma_smem_bytes(PL::TB, false, P.has_phase || P.reduce, NS);
-  auto kern = k_fwd_tma<PL, NS, SW>;
+  const size_t smem = tma_smem_bytes(PL::TB, false, (K & (kPH | kRED)) != 0, NS);
+  auto kern = k_fwd_tma<PL, NS, SW, K>;
   static int nb = 0;
   if (nb == 0) {
     const size_t mx = tma_smem_bytes(PL::TB, false, true, NS);
@@ -862,10 +860,10 @@ static cudaError_t launch_fwd_tma_t(const TmaFwdParams &P, cudaStream_t s, int n
   return cudaGetLastError();
 }
 
-template <class PL, int NS, int SW>
+template <class PL, int NS, int SW, int K>
 static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int nsm) {
-  const size_t smem = tma_smem_bytes(PL::TB, true, P.has_phase || P.init_lambda, NS);
-  auto kern = k_bwd_tma<PL, NS, SW>;
+  const size_t smem = tma_smem_bytes(PL::TB, true, (K & (kPH | kINIT)) != 0, NS);
+  auto kern = k_bwd_tma<PL, NS, SW, K>;
   static int nb = 0;
   if (nb == 0) {
     const size_t mx = tma_smem_bytes(PL::TB, true, true, NS);
@@ -885,18 +883,46 @@ static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int n
 #define QAOA_TMA_STAGES 1
 #endif
 
+template <class PL, int NS>
+static cudaError_t dispatch_fwd(const TmaFwdParams &P, cudaStream_t s, int nsm) {
+  const bool h1 = (P.s1.m[0] | P.s1.m[1] | P.s1.m[2]) != 0;
+  const bool h2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2]) != 0;
+  const int k = (h1 ? kH1 : 0) | (P.has_phase ? kPH : 0) | (h2 ? kH2 : 0) | (P.reduce ? kRED : 0);
+  switch (k) {  // the kinds the forward schedules produce
+    case kPH | kH2: return launch_fwd_tma_t<PL, NS, 128, kPH | kH2>(P, s, nsm);
+    case kPH | kH2 | kRED: return launch_fwd_tma_t<PL, NS, 128, kPH | kH2 | kRED>(P, s, nsm);
+    case kH2: return launch_fwd_tma_t<PL, NS, 128, kH2>(P, s, nsm);
+    case kH1 | kPH | kH2: return launch_fwd_tma_t<PL, NS, 128, kH1 | kPH | kH2>(P, s, nsm);
+    case kH1: return launch_fwd_tma_t<PL, NS, 128, kH1>(P, s, nsm);
+    case kH1 | kRED: return launch_fwd_tma_t<PL, NS, 128, kH1 | kRED>(P, s, nsm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <class PL, int NS>
+static cudaError_t dispatch_bwd(const TmaBwdParams &P, cudaStream_t s, int nsm) {
+  const bool h2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2]) != 0;
+  const int k = (P.has_phase ? kPH : 0) | (h2 ? kH2 : 0) | (P.init_lambda ? kINIT : 0);
+  switch (k) {  // the kinds the adjoint schedules produce
+    case 0: return launch_bwd_tma_t<PL, NS, 128, 0>(P, s, nsm);
+    case kINIT: return launch_bwd_tma_t<PL, NS, 128, kINIT>(P, s, nsm);
+    case kPH | kH2: return launch_bwd_tma_t<PL, NS, 128, kPH | kH2>(P, s, nsm);
+    case kPH: return launch_bwd_tma_t<PL, NS, 128, kPH>(P, s, nsm);
+    case kPH | kINIT: return launch_bwd_tma_t<PL, NS, 128, kPH | kINIT>(P, s, nsm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm) {
   constexpr int NS = QAOA_TMA_STAGES;
-  return high ? launch_fwd_tma_t<PlanTmaF13High, NS, 128>(P, s, nsm)
-              : launch_fwd_tma_t<PlanTmaF13Low, NS, 128>(P, s, nsm);
+  if (P.c != 4) return cudaErrorInvalidValue;  // 16-amplitude segments only
+  return high ? dispatch_fwd<PlanTmaF13High, NS>(P, s, nsm) : dispatch_fwd<PlanTmaF13Low, NS>(P, s, nsm);
 }
 
 cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {
   constexpr int NS = QAOA_TMA_STAGES;
-  if (!high) return launch_bwd_tma_t<PlanTmaB12Low, NS, 128>(P, s, nsm);
-  // 8-amplitude (64-byte) segments: HIGH passes rotate 9 qubits
-  return P.c == 3 ? launch_bwd_tma_t<PlanTmaB12High, NS, 64>(P, s, nsm)
-                  : launch_bwd_tma_t<PlanTmaB12High, NS, 128>(P, s, nsm);
+  if (P.c != 4) return cudaErrorInvalidValue;  // 16-amplitude segments only
+  return high ? dispatch_bwd<PlanTmaB12High, NS>(P, s, nsm) : dispatch_bwd<PlanTmaB12Low, NS>(P, s, nsm);
 }
 
 }  // namespace qaoa
