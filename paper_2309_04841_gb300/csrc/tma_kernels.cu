@@ -345,9 +345,10 @@ __device__ __forceinline__ void csum(double (&a)[K], double *red) {
     }
 }
 
-// After the tile loop: the last CTA sums the per-tile partials in tile order.
+// After the tile loop: the last CTA sums the per-CTA partials in CTA order
+// (deterministic for a given grid; the grid depends only on the GPU and n).
 template <int K, class Fin>
-__device__ __forceinline__ void final_reduce(const double *partials, uint64_t ntiles,
+__device__ __forceinline__ void final_reduce(const double *partials, uint64_t nparts,
                                              unsigned *counter, double *red, Fin fin) {
   __shared__ int am_last;
   __threadfence();
@@ -359,7 +360,7 @@ __device__ __forceinline__ void final_reduce(const double *partials, uint64_t nt
   double a[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) a[k] = 0.0;
-  for (uint64_t t = threadIdx.x; t < ntiles; t += 256)
+  for (uint64_t t = threadIdx.x; t < nparts; t += 256)
 #pragma unroll
     for (int k = 0; k < K; ++k) a[k] += __ldcg(partials + t * K + k);
   csum<K>(a, red);
@@ -491,18 +492,19 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     }
   } else {
     // ---------------- compute warps
+    double acc_e = 0.0, acc_o = 0.0;  // this thread's energy / overlap terms
     for (int i = 0;; ++i) {
       const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
       if (T >= P.ntiles) break;
       const int s = i % NS;
-      // every compute thread takes the same decision after a timeout, so no
-      // thread is left waiting at a barrier the others skipped
+      // A timed-out wait flags the abort and still runs this tile (on stale
+      // data) through the same barriers as every other thread; all threads
+      // see the flag after those barriers and leave together.
+      if (s_abort) break;
       if (!mbar_wait(&full[s], (i / NS) & 1)) {
         s_abort = 1;
         atomicExch(P.err, 1u);
       }
-      cbar();
-      if (s_abort) break;
       float2 *buf = reinterpret_cast<float2 *>(base + s * L.tile_bytes);
       const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off + s * L.cost_bytes);
       float2 v[NREG];
@@ -580,19 +582,23 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
         }
       }
       if constexpr (RED) {
-        double a[2] = {(double)e, (double)o};
-        csum<2>(a, red);
-        if (tid == 0) {
-          P.partials[T * 2] = a[0];
-          P.partials[T * 2 + 1] = a[1];
-        }
+        acc_e += (double)e;
+        acc_o += (double)o;
       }
     }
     if (NS == 1 && tid == 0) bulk_wait0();
+    if constexpr (RED) {
+      double a[2] = {acc_e, acc_o};
+      csum<2>(a, red);
+      if (tid == 0) {
+        P.partials[blockIdx.x * 2] = a[0];
+        P.partials[blockIdx.x * 2 + 1] = a[1];
+      }
+    }
   }
   if constexpr (RED) {
     double *out = P.out;
-    final_reduce<2>(P.partials, P.ntiles, P.counter, red, [out](double(&a)[2]) {
+    final_reduce<2>(P.partials, gridDim.x, P.counter, red, [out](double(&a)[2]) {
       out[0] = a[0];
       out[1] = a[1];
     });
@@ -679,16 +685,19 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       bulk_wait0();
     }
   } else {
+    double acc1 = 0.0, accg = 0.0, acc2 = 0.0;  // this thread's gradient terms
     for (int i = 0;; ++i) {
       const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
       if (T >= P.ntiles) break;
       const int s = i % NS;
+      // A timed-out wait flags the abort and still runs this tile (on stale
+      // data) through the same barriers as every other thread; all threads
+      // see the flag after those barriers and leave together.
+      if (s_abort) break;
       if (!mbar_wait(&full[s], (i / NS) & 1)) {
         s_abort = 1;
         atomicExch(P.err, 1u);
       }
-      cbar();
-      if (s_abort) break;
       float2 *bv = reinterpret_cast<float2 *>(base + s * L.tile_bytes);
       float2 *bw = reinterpret_cast<float2 *>(base + L.lam_off + s * L.tile_bytes);
       const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off + s * L.cost_bytes);
@@ -774,18 +783,21 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
           }
         }
       }
-      double a[3] = {(double)a1, (double)ag, (double)a2};
-      csum<3>(a, red);
-      if (tid == 0) {
-        P.partials[T * 3] = a[0];
-        P.partials[T * 3 + 1] = a[1];
-        P.partials[T * 3 + 2] = a[2];
-      }
+      acc1 += (double)a1;
+      accg += (double)ag;
+      acc2 += (double)a2;
     }
     if (NS == 1 && tid == 0) bulk_wait0();
+    double a[3] = {acc1, accg, acc2};
+    csum<3>(a, red);
+    if (tid == 0) {
+      P.partials[blockIdx.x * 3] = a[0];
+      P.partials[blockIdx.x * 3 + 1] = a[1];
+      P.partials[blockIdx.x * 3 + 2] = a[2];
+    }
   }
   double *o1 = P.out_b1, *og = P.out_g, *o2 = P.out_b2;
-  final_reduce<3>(P.partials, P.ntiles, P.counter, red, [=](double(&a)[3]) {
+  final_reduce<3>(P.partials, gridDim.x, P.counter, red, [=](double(&a)[3]) {
     if (o1) *o1 += 2.0 * a[0];
     if (og) *og += 2.0 * a[1];
     if (o2) *o2 += 2.0 * a[2];
