@@ -202,6 +202,14 @@ std::vector<Group> plan_groups(int n, int TB, int chigh = kHighC) {
   return gs;
 }
 
+// Groups for the TMA passes: 32-amplitude (256-byte) segments when that
+// costs no extra group, 16-amplitude (128-byte) ones otherwise.
+std::vector<Group> tma_groups(int n, int TB) {
+  std::vector<Group> g4 = plan_groups(n, TB, 4);
+  std::vector<Group> g5 = plan_groups(n, TB, 5);
+  return g5.size() <= g4.size() ? g5 : g4;
+}
+
 Geom make_geom(int n, const Group &G, int TB) {
   Geom g;
   g.n = n;
@@ -519,7 +527,7 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
   using Low = PlanTmaF13Low;
   using High = PlanTmaF13High;
   const int TB = Low::TB;
-  const std::vector<Group> gs = plan_groups(n, TB);
+  const std::vector<Group> gs = tma_groups(n, TB);
   const std::vector<PassOp> ops = forward_schedule((int)gs.size(), p, init_plus != 0, d_out != nullptr);
   const int nsm = num_sms();
   if (d_out) CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
@@ -531,7 +539,7 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
     const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
-    CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, c == 4 ? 128 : 64), "tensor map (state)");
+    CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, c == 3 ? 64 : 128), "tensor map (state)");
     CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, 4, 0), "tensor map (cost)");
     P.ntiles = 1ull << (n - TB);
     P.h = h;
@@ -589,8 +597,8 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
   using Low = PlanTmaB12Low;
   using High = PlanTmaB12High;
   const int TB = Low::TB;
-  // 16-amplitude (128-byte) segments: 8-amplitude ones halve the HBM efficiency
-  const std::vector<Group> gs = plan_groups(n, TB, kHighC);
+  // 16- or 32-amplitude segments (8-amplitude ones halve the HBM efficiency)
+  const std::vector<Group> gs = tma_groups(n, TB);
   const std::vector<PassOp> ops = adjoint_schedule((int)gs.size(), p);
   const int nsm = num_sms();
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
@@ -602,7 +610,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
     const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
-    const int sw = c == 4 ? 128 : 64;
+    const int sw = c == 3 ? 64 : 128;
     CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, sw), "tensor map (psi)");
     CK(make_tile_map(&P.map_lam, lam, n, TB, h, c, 8, sw), "tensor map (lambda)");
     CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, 4, 0), "tensor map (cost)");

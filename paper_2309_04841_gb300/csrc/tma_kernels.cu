@@ -71,21 +71,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   return true;
 }
 
-__device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, int c1, int c4,
-                                         uint64_t *bar) {
+// Tile coordinates in the 5-D tensor-map view: (0, x1, x2, 0, x4).
+struct TC {
+  int x1, x2, x4;
+};
+
+__device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, TC c, uint64_t *bar) {
   asm volatile(
       "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(0), "r"(0), "r"(c4),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c.x1), "r"(c.x2), "r"(0), "r"(c.x4),
       "r"(smem_u32(bar))
       : "memory");
 }
 
-__device__ __forceinline__ void tma_store(const CUtensorMap *map, const void *src, int c1, int c4) {
+__device__ __forceinline__ void tma_store(const CUtensorMap *map, const void *src, TC c) {
   asm volatile(
       "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group"
       " [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
-      "r"(smem_u32(src)), "r"(0), "r"(c1), "r"(0), "r"(0), "r"(c4)
+      "r"(smem_u32(src)), "r"(0), "r"(c.x1), "r"(c.x2), "r"(0), "r"(c.x4)
       : "memory");
 }
 
@@ -449,16 +453,21 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
   }
   __syncthreads();
 
-  auto coords = [&](uint64_t T, int &c1, int &c4) {
-    c1 = (int)(T & ((1ull << midbits) - 1ull));
-    c4 = (int)(T >> midbits);
+  // 16-amplitude segments: the outer bits between the segments are view
+  // dimension 1; 32-amplitude segments (bit 4 is view dimension 1): dimension 2
+  auto coords = [&](uint64_t T) {
+    const int mid = (int)(T & ((1ull << midbits) - 1ull));
+    TC c;
+    c.x1 = P.c == 4 ? mid : 0;
+    c.x2 = P.c == 4 ? 0 : mid;
+    c.x4 = (int)(T >> midbits);
+    return c;
   };
   auto issue = [&](uint64_t T, int s) {
-    int c1, c4;
-    coords(T, c1, c4);
+    const TC c = coords(T);
     mbar_expect_tx(&full[s], (P.init_plus ? 0u : L.tile_bytes) + (need_cost ? L.cost_bytes : 0u));
-    if (!P.init_plus) tma_load(base + s * L.tile_bytes, &P.map_psi, c1, c4, &full[s]);
-    if (need_cost) tma_load(base + L.cost_off + s * L.cost_bytes, &P.map_cost, c1, c4, &full[s]);
+    if (!P.init_plus) tma_load(base + s * L.tile_bytes, &P.map_psi, c, &full[s]);
+    if (need_cost) tma_load(base + L.cost_off + s * L.cost_bytes, &P.map_cost, c, &full[s]);
   };
 
   if (tid == (NS == 1 ? 0 : 256))
@@ -478,9 +487,8 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
           atomicExch(P.err, 1u);
           break;
         }
-        int c1, c4;
-        coords(T, c1, c4);
-        tma_store(&P.map_psi, base + s * L.tile_bytes, c1, c4);
+        const TC c = coords(T);
+        tma_store(&P.map_psi, base + s * L.tile_bytes, c);
         bulk_commit();
         const uint64_t T2 = T + (uint64_t)NS * gridDim.x;
         if (T2 < P.ntiles) {
@@ -570,9 +578,8 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       } else {
         cbar();
         if (tid == 0) {
-          int c1, c4;
-          coords(T, c1, c4);
-          tma_store(&P.map_psi, buf, c1, c4);
+          const TC c = coords(T);
+          tma_store(&P.map_psi, buf, c);
           bulk_commit();
           const uint64_t T2 = T + gridDim.x;
           if (T2 < P.ntiles) {
@@ -638,24 +645,28 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
   }
   __syncthreads();
 
-  auto coords = [&](uint64_t T, int &c1, int &c4) {
-    c1 = (int)(T & ((1ull << midbits) - 1ull));
-    c4 = (int)(T >> midbits);
+  // 16-amplitude segments: the outer bits between the segments are view
+  // dimension 1; 32-amplitude segments (bit 4 is view dimension 1): dimension 2
+  auto coords = [&](uint64_t T) {
+    const int mid = (int)(T & ((1ull << midbits) - 1ull));
+    TC c;
+    c.x1 = P.c == 4 ? mid : 0;
+    c.x2 = P.c == 4 ? 0 : mid;
+    c.x4 = (int)(T >> midbits);
+    return c;
   };
   auto issue = [&](uint64_t T, int s) {
-    int c1, c4;
-    coords(T, c1, c4);
+    const TC c = coords(T);
     mbar_expect_tx(&full[s], L.tile_bytes + (INIT ? 0u : L.tile_bytes) +
                                  (need_cost ? L.cost_bytes : 0u));
-    tma_load(base + s * L.tile_bytes, &P.map_psi, c1, c4, &full[s]);
-    if (!INIT) tma_load(base + L.lam_off + s * L.tile_bytes, &P.map_lam, c1, c4, &full[s]);
-    if (need_cost) tma_load(base + L.cost_off + s * L.cost_bytes, &P.map_cost, c1, c4, &full[s]);
+    tma_load(base + s * L.tile_bytes, &P.map_psi, c, &full[s]);
+    if (!INIT) tma_load(base + L.lam_off + s * L.tile_bytes, &P.map_lam, c, &full[s]);
+    if (need_cost) tma_load(base + L.cost_off + s * L.cost_bytes, &P.map_cost, c, &full[s]);
   };
   auto store = [&](uint64_t T, int s) {
-    int c1, c4;
-    coords(T, c1, c4);
-    tma_store(&P.map_psi, base + s * L.tile_bytes, c1, c4);
-    tma_store(&P.map_lam, base + L.lam_off + s * L.tile_bytes, c1, c4);
+    const TC c = coords(T);
+    tma_store(&P.map_psi, base + s * L.tile_bytes, c);
+    tma_store(&P.map_lam, base + L.lam_off + s * L.tile_bytes, c);
     bulk_commit();
   };
 
@@ -836,13 +847,29 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
                           int swizzle_bytes) {
   EncodeFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
-  const int hi = tb - c - 8;  // extra high-segment bits beyond 256 rows
-  if (hi < 0 || h < c || n < h + tb - c) return cudaErrorInvalidValue;
-  cuuint64_t dims[5] = {1ull << c, 1ull << (h - c), 256, 1ull << hi, 1ull << (n - h - (tb - c))};
   const cuuint64_t e = (cuuint64_t)esz;
-  cuuint64_t strides[4] = {(1ull << c) * e, (1ull << h) * e, (1ull << (h + 8)) * e,
-                           (1ull << (h + 8 + hi)) * e};
-  cuuint32_t box[5] = {(cuuint32_t)(1u << c), 1, 256, (cuuint32_t)(1u << hi), 1};
+  cuuint64_t dims[5], strides[4];
+  cuuint32_t box[5];
+  if (c == 5) {
+    // 32 contiguous amplitudes as [16][2] (a swizzled box row is at most
+    // 128 bytes), then the outer bits 5..h-1, the rows, the rest
+    const int rows = tb - 5;
+    if (h < 5 || rows > 8 || n < h + rows) return cudaErrorInvalidValue;
+    const cuuint64_t d[5] = {16, 2, 1ull << (h - 5), 1ull << rows, 1ull << (n - h - rows)};
+    const cuuint64_t st[4] = {16 * e, 32 * e, (1ull << h) * e, (1ull << (h + rows)) * e};
+    const cuuint32_t bx[5] = {16, 2, 1, (cuuint32_t)(1u << rows), 1};
+    for (int i = 0; i < 5; ++i) dims[i] = d[i], box[i] = bx[i];
+    for (int i = 0; i < 4; ++i) strides[i] = st[i];
+  } else {
+    const int hi = tb - c - 8;  // extra high-segment bits beyond 256 rows
+    if (hi < 0 || h < c || n < h + tb - c) return cudaErrorInvalidValue;
+    const cuuint64_t d[5] = {1ull << c, 1ull << (h - c), 256, 1ull << hi, 1ull << (n - h - (tb - c))};
+    const cuuint64_t st[4] = {(1ull << c) * e, (1ull << h) * e, (1ull << (h + 8)) * e,
+                              (1ull << (h + 8 + hi)) * e};
+    const cuuint32_t bx[5] = {(cuuint32_t)(1u << c), 1, 256, (cuuint32_t)(1u << hi), 1};
+    for (int i = 0; i < 5; ++i) dims[i] = d[i], box[i] = bx[i];
+    for (int i = 0; i < 4; ++i) strides[i] = st[i];
+  }
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   const CUtensorMapDataType dt = esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
   const CUtensorMapSwizzle sw = swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
@@ -927,13 +954,13 @@ static cudaError_t dispatch_bwd(const TmaBwdParams &P, cudaStream_t s, int nsm) 
 
 cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm) {
   constexpr int NS = QAOA_TMA_STAGES;
-  if (P.c != 4) return cudaErrorInvalidValue;  // 16-amplitude segments only
+  if (P.c != 4 && P.c != 5) return cudaErrorInvalidValue;  // 16- or 32-amplitude segments
   return high ? dispatch_fwd<PlanTmaF13High, NS>(P, s, nsm) : dispatch_fwd<PlanTmaF13Low, NS>(P, s, nsm);
 }
 
 cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {
   constexpr int NS = QAOA_TMA_STAGES;
-  if (P.c != 4) return cudaErrorInvalidValue;  // 16-amplitude segments only
+  if (P.c != 4 && P.c != 5) return cudaErrorInvalidValue;  // 16- or 32-amplitude segments
   return high ? dispatch_bwd<PlanTmaB12High, NS>(P, s, nsm) : dispatch_bwd<PlanTmaB12Low, NS>(P, s, nsm);
 }
 
