@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--cpu-sample-n", type=int, default=22,
                     help="n of the oracle sample timed for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=400)
     return ap.parse_args()
 
 
@@ -296,6 +298,88 @@ def run_ours(a, ws, rank, local):
     return line, clk.summary()
 
 
+# ------------------------------------------------------------ serving
+
+def serving_bench(count=400, nmin=16, nmax=26):
+    """Serving loop vs the plain per-request path on one request stream."""
+    import numpy as np
+    import torch
+
+    from paper_2309_04841_gb300 import inputs as I
+    from paper_2309_04841_gb300 import qaoa as Q
+
+    reqs = I.serving_stream(count, nmin=nmin, nmax=nmax)
+    # plain path: one qaoa_grad after another on one stream, cost vectors cached
+    cache = {}
+    service = []
+    for r in reqs:
+        k = (r["problem"], r["n"], r["key"])
+        if k not in cache:
+            fd = Q.labs_costs(r["n"]) if r["problem"] == 0 else Q.maxcut_costs(r["n"], r["edges"], r["weights"])
+            cache[k] = (fd, Q.cost_stats_compute(fd))
+        fd, st = cache[k]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = Q.grad(fd, st, r["gammas"], r["betas"])
+        out.cpu()
+        service.append(time.perf_counter() - t)
+    del cache
+    torch.cuda.empty_cache()
+    service = np.array(service)
+    plain_tput = count / service.sum()
+
+    def sub(srv, r):
+        return srv.submit(r["problem"], r["n"], r["gammas"], r["betas"], edges=r["edges"],
+                          weights=r["weights"], key=r["key"], want_grad=True)
+
+    free, _ = torch.cuda.mem_get_info()
+    arena = int(min(free * 0.6, 96 << 30))
+    srv = Q.Server(arena, max_inflight=8)
+    for r in reqs[:8]:  # warm the cost-vector cache and the kernels
+        srv.wait(sub(srv, r), r["p"])
+    # saturated: everything submitted at once
+    t0 = time.perf_counter()
+    ts = [sub(srv, r) for r in reqs]
+    for t, r in zip(ts, reqs):
+        srv.wait(t, r["p"])
+    sat_tput = count / (time.perf_counter() - t0)
+    srv.close()
+    # open loop: Poisson arrivals at 80% of the saturated throughput
+    rate = 0.8 * sat_tput
+    arr = I.poisson_arrivals(count, rate)
+    srv = Q.Server(arena, max_inflight=8)
+    for r in reqs[:8]:
+        srv.wait(sub(srv, r), r["p"])
+    base = time.perf_counter()
+    ts = []
+    for a, r in zip(arr, reqs):
+        d = base + a - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        ts.append(sub(srv, r))
+    lat = []
+    for t, r in zip(ts, reqs):
+        res = srv.wait(t, r["p"])
+        lat.append(res["finish_s"] - res["submit_s"])
+    srv.close()
+    lat = np.sort(np.array(lat)) * 1000
+    # the plain path under the same arrivals: a FIFO single-server queue
+    fin, plat = 0.0, []
+    for a, s in zip(arr, service):
+        fin = max(fin, a) + s
+        plat.append(fin - a)
+    plat = np.sort(np.array(plat)) * 1000
+    pct = lambda v, q: float(v[min(len(v) - 1, int(round(q * (len(v) - 1))))])
+    return {"requests": count,
+            "recipe": (f"objective+gradient requests, n ~ U{{{nmin}..{nmax}}} (MaxCut rounded up to even), "
+                       "p ~ U{1..40}, LABS or MaxCut 3-regular 50/50 (4 graphs per n), complex64; "
+                       f"Poisson arrivals at 0.8 x the saturated server throughput"),
+            "server": {"evals_per_s_saturated": sat_tput, "arrival_rate_per_s": rate,
+                       "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99)},
+            "plain_per_request": {"evals_per_s": plain_tput, "p50_ms": pct(plat, 0.5),
+                                  "p99_ms": pct(plat, 0.99)}}
+
+
 # ------------------------------------------------------- reference arm
 
 def run_reference(a, ws, rank):
@@ -340,6 +424,8 @@ def main():
     line, clocks = run_ours(a, ws, rank, local)
     if rank == 0:
         line["clocks"] = clocks
+        if not a.no_serving:
+            line["serving"] = serving_bench(a.serving_requests)
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(a.cpu_sample_n, line["config"]["p"],
                                                 line["config"]["n"])

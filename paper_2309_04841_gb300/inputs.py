@@ -209,3 +209,35 @@ def workload_graph(w):
     if w["problem"] == "gnp":
         return maxcut_gnp(w["n"], 0.5, w["graph_seed"], w["weight_seed"])
     return None
+
+
+def serving_stream(count, seed=9, nmin=16, nmax=26, pmax=40, graphs_per_n=4):
+    """Request stream of the serving workload: n ~ U{nmin..nmax}, p ~ U{1..pmax},
+    LABS or MaxCut 3-regular (50/50; each n draws from a pool of
+    `graphs_per_n` graphs so cost vectors repeat), gamma ~ U[0, 0.1),
+    beta ~ U[0, pi).  Returns a list of request dicts."""
+    r = randint(seed, 4 * count, 1 << 30)
+    out = []
+    for i in range(count):
+        n = nmin + int(r[4 * i]) % (nmax - nmin + 1)
+        p = 1 + int(r[4 * i + 1]) % pmax
+        maxcut = int(r[4 * i + 2]) % 2 == 1
+        pool = int(r[4 * i + 3]) % graphs_per_n
+        g = angles(p, 1000 + 2 * i, 0.0, 0.1)
+        b = angles(p, 1001 + 2 * i, 0.0, math.pi)
+        if maxcut:
+            n += n % 2
+            edges, w = maxcut_3reg(n, graph_seed=100 + pool, weighted=False)
+            out.append(dict(problem=1, n=n, p=p, gammas=g, betas=b, edges=edges, weights=w,
+                            key=pool))
+        else:
+            out.append(dict(problem=0, n=n, p=p, gammas=g, betas=b, edges=None, weights=None,
+                            key=0))
+    return out
+
+
+def poisson_arrivals(count, rate, seed=19):
+    """Arrival times (s) of a Poisson process with the given rate."""
+    u = uniform(seed, count)
+    gaps = -np.log1p(-u) / rate
+    return np.cumsum(gaps)
