@@ -140,6 +140,30 @@ void make_phase(PhaseData<Real> &ph, double g, qaoa_cost_type ct, const qaoa_cos
   }
 }
 
+// Digit tables of exp(-i g f) for the TMA passes (layout in PhaseDigits).
+void make_phase(PhaseDigits &ph, double g, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                std::complex<double> scale) {
+  memset(&ph, 0, sizeof(ph));
+  const double range = stats ? stats->f_max - stats->f_min : 1e300;
+  if (ct == QAOA_COST_I32 && stats && range >= 0 && range < 32768.0) {
+    ph.mode = 0;
+    ph.fmin = (int)stats->f_min;
+    for (int j = 0; j < 32; ++j) {
+      const double a0 = g * (double)j, a1 = g * (double)(32 * j);
+      const double a2 = g * ((double)stats->f_min + 1024.0 * (double)j);
+      const std::complex<double> z2 = std::complex<double>(cos(a2), -sin(a2)) * scale;
+      ph.d[0][j] = make_float2((float)cos(a0), (float)-sin(a0));
+      ph.d[1][j] = make_float2((float)cos(a1), (float)-sin(a1));
+      ph.d[2][j] = make_float2((float)z2.real(), (float)z2.imag());
+    }
+  } else {
+    ph.mode = 1;
+    const double g2 = g / kTwoPi;
+    ph.g_hi = (float)g2;
+    ph.g_lo = (float)(g2 - (double)ph.g_hi);
+  }
+}
+
 // Rotation schedule of one sweep over the tile bits in `set`: each bit goes
 // to the first round (in the kernel's traversal order) holding it in a
 // register; bits no round holds in a register go to the first round holding
@@ -557,7 +581,7 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
     P.has_phase = op.lp >= 0;
     if (P.has_phase) {
       // the pending scale rides on the phase multiply
-      make_phase<float>(P.ph, gam[op.lp], ct, stats, sig);
+      make_phase(P.ph, gam[op.lp], ct, stats, sig);
       P.scl_phase = f2c(sig);
       sig = 1.0;
     }
@@ -635,7 +659,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
       P.has_phase = 1;
       P.wg = (float)std::norm(sig);
       // the un-phase multiply also pays the pending scale
-      make_phase<float>(P.ph, -gam[op.lp], ct, stats, sig);
+      make_phase(P.ph, -gam[op.lp], ct, stats, sig);
       P.scl_phase = f2c(sig);
       sig = 1.0;
       P.out_g = d_grad_g + op.lp;

@@ -72,6 +72,23 @@ static_assert(PlanTmaB12Low::valid() && PlanTmaB12High::valid(), "bad TMA B12 pl
 // (the adjoint uses -b), |t|, |u| <= 1; the host tracks the product of the
 // sigmas and folds it into the next phase multiply (scl_phase, or the phase
 // table) or applies it at the end of the pass (scl_end).
+// Phase factors of the TMA passes.  Mode 0 (integer costs, f_max - f_min <
+// 2^15): with d = f - fmin split into three 5-bit digits,
+//   exp(-i g f) = D0[d & 31] * D1[(d >> 5) & 31] * D2[d >> 10],
+// D2 also carrying exp(-i g fmin) and the pending scale.  Shared memory holds
+// each table as 16 interleaved copies, so the 16 lanes of a half-warp read 16
+// different bank pairs whatever their costs.  Mode 1: computed from g / 2pi =
+// g_hi + g_lo (float-float).
+struct PhaseDigits {
+  int mode;
+  int fmin;
+  float g_hi, g_lo;
+  float2 d[3][32];
+};
+
+constexpr int kPhaseCopies = 16;
+constexpr int kPhaseTabEntries = 3 * 32 * kPhaseCopies;
+
 struct alignas(64) TmaFwdParams {
   CUtensorMap map_psi;   // state, 8-byte elements, 128-byte swizzle
   CUtensorMap map_cost;  // cost vector, 4-byte elements
@@ -89,7 +106,7 @@ struct alignas(64) TmaFwdParams {
   unsigned *counter;
   double *out;
   unsigned *err;
-  PhaseData<float> ph;
+  PhaseDigits ph;
 };
 
 struct alignas(64) TmaBwdParams {
@@ -107,7 +124,7 @@ struct alignas(64) TmaBwdParams {
   unsigned *counter;
   double *out_b1, *out_g, *out_b2;
   unsigned *err;
-  PhaseData<float> ph;
+  PhaseDigits ph;
 };
 
 cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, int c, int esz,

@@ -268,11 +268,16 @@ __device__ __forceinline__ void xp(float2 (&v)[PL::NREG], float2 *buf) {
 }
 
 // exp(-i g f) from the raw 32-bit cost word (int32 or float32).
-__device__ __forceinline__ float2 phase_of(const PhaseData<float> &ph, int kind, const float2 *tlo,
-                                           const float2 *thi, uint32_t word) {
+__device__ __forceinline__ float2 phase_of(const PhaseDigits &ph, int kind, const float2 *tab,
+                                           uint32_t word) {
   if (ph.mode == 0) {
-    const uint32_t v = (uint32_t)((int)word - ph.fmin);
-    return cmulf(thi[min(v >> 8, 255u)], tlo[v & 255u]);
+    // three conflict-free lookups: this lane's copy of each digit table
+    const uint32_t d = (uint32_t)((int)word - ph.fmin);
+    const uint32_t q = threadIdx.x & (kPhaseCopies - 1);
+    const float2 a = tab[((d & 31u) << 4) | q];
+    const float2 b = tab[((32u + ((d >> 5) & 31u)) << 4) | q];
+    const float2 c = tab[((64u + min(d >> 10, 31u)) << 4) | q];
+    return cmulf(cmulf(a, b), c);
   }
   float fh, fl;
   if (kind == kCostI32) {
@@ -292,6 +297,13 @@ __device__ __forceinline__ float2 phase_of(const PhaseData<float> &ph, int kind,
   return f2(cs, -sn);
 }
 
+// Shared-memory copy of the digit tables: entry j of table k, copy q at
+// ((32 k + j) * 16 + q).
+template <int NT>
+__device__ __forceinline__ void fill_phase_tab(float2 *tab, const PhaseDigits &ph) {
+  for (int i = threadIdx.x; i < kPhaseTabEntries; i += NT) tab[i] = ph.d[i >> 9][(i >> 4) & 31];
+}
+
 __device__ __forceinline__ float cost_val(int kind, uint32_t word) {
   return kind == kCostI32 ? (float)(int)word : __uint_as_float(word);
 }
@@ -299,17 +311,17 @@ __device__ __forceinline__ float cost_val(int kind, uint32_t word) {
 // v <- v * exp(-i g f) (* scl in computed mode; table mode has it folded in).
 template <class PL, int R>
 __device__ __forceinline__ void phase_round(float2 (&v)[PL::NREG], const uint32_t *cb,
-                                            const PhaseData<float> &ph, int kind,
-                                            const float2 *tlo, const float2 *thi, float2 scl) {
+                                            const PhaseDigits &ph, int kind, const float2 *tab,
+                                            float2 scl) {
   const uint32_t tt = thr_tile<PL, R>();
   if (ph.mode == 0) {
 #pragma unroll
     for (int r = 0; r < PL::NREG; ++r)
-      v[r] = cmulf(v[r], phase_of(ph, kind, tlo, thi, cb[tt | pdep(r, PL::reg(R))]));
+      v[r] = cmulf(v[r], phase_of(ph, kind, tab, cb[tt | pdep(r, PL::reg(R))]));
   } else {
 #pragma unroll
     for (int r = 0; r < PL::NREG; ++r)
-      v[r] = cmulf(v[r], cmulf(scl, phase_of(ph, kind, tlo, thi, cb[tt | pdep(r, PL::reg(R))])));
+      v[r] = cmulf(v[r], cmulf(scl, phase_of(ph, kind, tab, cb[tt | pdep(r, PL::reg(R))])));
   }
 }
 
@@ -388,7 +400,7 @@ __device__ __forceinline__ Lay layout(uint32_t tile_elems, bool two, bool cost, 
   L.cost_off = L.lam_off + (two ? ns * L.tile_bytes : 0u);
   L.cost_bytes = cost ? tile_elems * 4u : 0u;
   L.tab_off = L.cost_off + ns * L.cost_bytes;
-  L.bar_off = L.tab_off + 512u * 8u;
+  L.bar_off = L.tab_off + (uint32_t)kPhaseTabEntries * 8u;
   L.red_off = L.bar_off + 32u;
   return L;
 }
@@ -402,7 +414,8 @@ __device__ __forceinline__ unsigned char *aligned_base(unsigned char *raw) {
 
 size_t tma_smem_bytes(int tb, bool two, bool cost, int ns) {
   const size_t te = (size_t)1 << tb;
-  return 1024 + ns * te * 8 * (two ? 2 : 1) + (cost ? ns * te * 4 : 0) + 512 * 8 + 32 + 8 * 3 * 8;
+  return 1024 + ns * te * 8 * (two ? 2 : 1) + (cost ? ns * te * 4 : 0) + kPhaseTabEntries * 8 + 32 +
+         8 * 3 * 8;
 }
 
 // ------------------------------------------------------------- forward
@@ -431,18 +444,14 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
   constexpr bool need_cost = PH || RED;
   unsigned char *base = aligned_base(smem_raw);
   const Lay L = layout(1u << PL::TB, false, need_cost, NS);
-  float2 *tlo = reinterpret_cast<float2 *>(base + L.tab_off), *thi = tlo + 256;
+  float2 *tab = reinterpret_cast<float2 *>(base + L.tab_off);
   uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off), *empty = full + 2;
   double *red = reinterpret_cast<double *>(base + L.red_off);
   const int tid = threadIdx.x;
   const int midbits = P.h - P.c;
   __shared__ int s_abort;
 
-  if (PH && P.ph.mode == 0)
-    for (int i = tid; i < 256; i += NT) {
-      tlo[i] = P.ph.tab_lo[i];
-      thi[i] = P.ph.tab_hi[i];
-    }
+  if (PH && P.ph.mode == 0) fill_phase_tab<NT>(tab, P.ph);
   if (tid == 0) {
     s_abort = 0;
     for (int s = 0; s < NS; ++s) {
@@ -534,7 +543,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
           rot_tan<EB>(v, P.s1.m[2], P.tau1, P.form1);
         if constexpr (SW == 64) rot_lanes<NREG>(v, P.s1.lm[2], P.tau1, P.form1);
         }
-        if constexpr (PH) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
+        if constexpr (PH) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tab, P.scl_phase);
         if constexpr (H2) {
           rot_tan<EB>(v, P.s2.m[NR - 1], P.tau2, P.form2);
         if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[NR - 1], P.tau2, P.form2);
@@ -548,7 +557,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
           if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
         }
       } else {
-        if constexpr (PH) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tlo, thi, P.scl_phase);
+        if constexpr (PH) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tab, P.scl_phase);
         rot_tan<EB>(v, P.s2.m[0], P.tau2, P.form2);
         if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
         xp<PL, 0, 1, SW>(v, buf);
@@ -623,18 +632,14 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
   constexpr bool need_cost = PH || INIT;
   unsigned char *base = aligned_base(smem_raw);
   const Lay L = layout(1u << PL::TB, true, need_cost, NS);
-  float2 *tlo = reinterpret_cast<float2 *>(base + L.tab_off), *thi = tlo + 256;
+  float2 *tab = reinterpret_cast<float2 *>(base + L.tab_off);
   uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off), *empty = full + 2;
   double *red = reinterpret_cast<double *>(base + L.red_off);
   const int tid = threadIdx.x;
   const int midbits = P.h - P.c;
   __shared__ int s_abort;
 
-  if (PH && P.ph.mode == 0)
-    for (int i = tid; i < 256; i += NT) {
-      tlo[i] = P.ph.tab_lo[i];
-      thi[i] = P.ph.tab_hi[i];
-    }
+  if (PH && P.ph.mode == 0) fill_phase_tab<NT>(tab, P.ph);
   if (tid == 0) {
     s_abort = 0;
     for (int s = 0; s < NS; ++s) {
@@ -749,7 +754,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
           const uint32_t word = cb[tt | pdep(r, PL::reg(NR - 1))];
           const float f = cost_val(P.cost_kind, word);
           ag += P.wg * f * (w[r].x * v[r].y - w[r].y * v[r].x);
-          float2 ph = phase_of(P.ph, P.cost_kind, tlo, thi, word);
+          float2 ph = phase_of(P.ph, P.cost_kind, tab, word);
           if (P.ph.mode != 0) ph = cmulf(ph, P.scl_phase);
           v[r] = cmulf(v[r], ph);
           w[r] = cmulf(w[r], ph);
