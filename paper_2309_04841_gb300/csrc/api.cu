@@ -526,17 +526,20 @@ struct TanRot {
   std::complex<double> sigma;
 };
 
+// Reduced form of exp(-i b X) in the twisted basis (b = -beta for the
+// adjoint): form 0 t = tan b, sigma = cos b; form 1 u = cot b, sigma = sin b.
 TanRot tan_rot(double beta, bool adjoint) {
-  const double c = cos(beta), s = sin(beta);
+  const double b = adjoint ? -beta : beta;
+  const double c = cos(b), s = sin(b);
   TanRot r;
   if (fabs(c) >= fabs(s)) {
     r.form = 0;
-    r.tau = (float)(adjoint ? -s / c : s / c);
+    r.tau = (float)(s / c);
     r.sigma = c;
   } else {
     r.form = 1;
-    r.tau = (float)(adjoint ? -c / s : c / s);
-    r.sigma = std::complex<double>(0.0, adjoint ? s : -s);
+    r.tau = (float)(c / s);
+    r.sigma = s;
   }
   return r;
 }
@@ -545,9 +548,11 @@ int popc8(uint8_t m) { return __builtin_popcount((unsigned)m); }
 
 float2 f2c(std::complex<double> z) { return make_float2((float)z.real(), (float)z.imag()); }
 
+// untwist: leave the final state in the standard basis (the adjoint instead
+// continues from the twisted one).
 qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
                         const double *gam, const double *bet, int p, void *state, int init_plus,
-                        const Ws &ws, double *d_out, cudaStream_t s) {
+                        const Ws &ws, double *d_out, bool untwist, cudaStream_t s) {
   using Low = PlanTmaF13Low;
   using High = PlanTmaF13High;
   const int TB = Low::TB;
@@ -563,7 +568,7 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
     const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
-    CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, c == 3 ? 64 : 128), "tensor map (state)");
+    CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, 128), "tensor map (state)");
     CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, 4, 0), "tensor map (cost)");
     P.ntiles = 1ull << (n - TB);
     P.h = h;
@@ -595,9 +600,12 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
     if (&op == &ops.back()) {
       P.end_scale = 1;
       P.scl_end = f2c(sig);
+      P.untwist = untwist;
       sig = 1.0;
     }
+    if (uses_lanes(P.s1) || uses_lanes(P.s2)) return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
     P.init_plus = op.init;
+    P.twist_in = &op == &ops.front() && !op.init;
     P.amp = (float)(1.0 / sqrt(ldexp(1.0, n)));
     P.reduce = op.reduce;
     P.fmin_d = stats ? stats->f_min : 0.0;
@@ -634,7 +642,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
     const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
-    const int sw = c == 3 ? 64 : 128;
+    const int sw = 128;
     CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, sw), "tensor map (psi)");
     CK(make_tile_map(&P.map_lam, lam, n, TB, h, c, 8, sw), "tensor map (lambda)");
     CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, 4, 0), "tensor map (cost)");
@@ -676,7 +684,9 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
       }
       P.out_b2 = d_grad_b + op.l2;
     }
+    if (uses_lanes(P.s1) || uses_lanes(P.s2)) return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
     P.init_lambda = op.init;
+    P.untwist = &op == &ops.back();
     P.partials = ws.partials;
     P.counter = ws.counter;
     P.err = ws.err;
@@ -983,7 +993,7 @@ qaoa_status qaoa_simulate(int n, const void *d_costs, qaoa_cost_type ct, const q
   }
   CK(cudaMemsetAsync(ws.err, 0, sizeof(unsigned), s), "memset error word");
   if (st == QAOA_C64 && tma_ok(ct))
-    return tma_forward(n, d_costs, ct, stats, gammas, betas, p, d_state, init_plus, ws, d_out, s);
+    return tma_forward(n, d_costs, ct, stats, gammas, betas, p, d_state, init_plus, ws, d_out, true, s);
   return st == QAOA_C64
              ? tiled_forward<float>(n, d_costs, ct, stats, gammas, betas, p, d_state, init_plus, ws, d_out, s)
              : tiled_forward<double>(n, d_costs, ct, stats, gammas, betas, p, d_state, init_plus, ws, d_out, s);
@@ -1045,7 +1055,7 @@ qaoa_status qaoa_grad(int n, const void *d_costs, qaoa_cost_type ct, const qaoa_
   CK(cudaMemsetAsync(d_out + 2, 0, sizeof(double) * 2 * (size_t)p, s), "memset grad");
   CK(cudaMemsetAsync(ws.err, 0, sizeof(unsigned), s), "memset error word");
   if (st == QAOA_C64 && tma_ok(ct)) {
-    r = tma_forward(n, d_costs, ct, stats, gammas, betas, p, d_state, 1, ws, d_out, s);
+    r = tma_forward(n, d_costs, ct, stats, gammas, betas, p, d_state, 1, ws, d_out, false, s);
     if (r != QAOA_OK) return r;
     return tma_backward(n, d_costs, ct, stats, gammas, betas, p, d_state, d_lambda, ws, d_out + 2,
                         d_out + 2 + p, s);

@@ -66,12 +66,16 @@ using PlanTmaB12High = Plan<12, 4, 256, 0, 2, 0x0F00, 0x001F, 0x00E0,
 static_assert(PlanTmaF13Low::valid() && PlanTmaF13High::valid(), "bad TMA F13 plan");
 static_assert(PlanTmaB12Low::valid() && PlanTmaB12High::valid(), "bad TMA B12 plan");
 
-// Rotations run in reduced ("tan") form: each exp(-i b X) = sigma * G with
-//   form 0: sigma = cos b,     G(a, b) = (a - i t b, b - i t a),  t = tan b
-//   form 1: sigma = -i sin b,  G(a, b) = (b + i u a, a + i u b),  u = cot b
+// The TMA passes hold vectors in the twisted basis s(x) = (-i)^popc(x) psi(x),
+// where exp(-i b X_q) acts on a pair as the real rotation
+// [[cos b, sin b], [-sin b, cos b]].  Rotations run in reduced ("tan") form,
+// exp(-i b X) = sigma * G with
+//   form 0: sigma = cos b,  G(a, b) = (a + t b, b - t a),  t = tan b
+//   form 1: sigma = sin b,  G(a, b) = (u a + b, u b - a),  u = cot b
 // (the adjoint uses -b), |t|, |u| <= 1; the host tracks the product of the
 // sigmas and folds it into the next phase multiply (scl_phase, or the phase
 // table) or applies it at the end of the pass (scl_end).
+
 // Phase factors of the TMA passes.  Mode 0 (integer costs, f_max - f_min <
 // 2^15): with d = f - fmin split into three 5-bit digits,
 //   exp(-i g f) = D0[d & 31] * D1[(d >> 5) & 31] * D2[d >> 10],
@@ -100,6 +104,8 @@ struct alignas(64) TmaFwdParams {
   float2 scl_phase, scl_end;
   int end_scale;
   int has_phase, init_plus, reduce;
+  int twist_in;  // first pass on a caller's state: into the twisted basis
+  int untwist;   // last pass (with end_scale): back to the standard basis
   float amp;
   double fmin_d;
   double *partials;
@@ -120,6 +126,7 @@ struct alignas(64) TmaBwdParams {
   float w1[4], w2[4]; // |scale|^2 weights of the inner products taken in each round
   float wg;           // |scale|^2 weight of the d/d gamma inner product
   int has_phase, init_lambda;
+  int untwist;  // last pass: psi back to the standard basis
   double *partials;
   unsigned *counter;
   double *out_b1, *out_g, *out_b2;

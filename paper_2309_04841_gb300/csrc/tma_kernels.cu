@@ -120,9 +120,19 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return f2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// Reduced-form rotation of the masked register bits (see TmaFwdParams).
+// ---- twisted basis
+// The passes keep psi (and lambda) as s(x) = (-i)^popc(x) psi(x).  In that
+// basis exp(-i b X_q) is the real rotation [[cos b, sin b], [-sin b, cos b]]
+// on each pair (s(x), s(x | 2^q)), applied alike to both components, so one
+// pair update is two packed fp32x2 FMAs.  Diagonal operators (the phase, f,
+// |.|^2) are unchanged.  Reduced (tangent) forms, the scale sigma (real) left
+// to the host:
+//   form 0: sigma = cos b, (a, b) <- (a + t b, b - t a),  t = tan b
+//   form 1: sigma = sin b, (a, b) <- (u a + b, u b - a),  u = cot b
+// (the adjoint uses -b); |t|, |u| <= 1.
 template <int EB>
-__device__ __forceinline__ void rot_tan(float2 (&v)[1 << EB], uint32_t m, float tau, int form) {
+__device__ __forceinline__ void rot_tw(float2 (&v)[1 << EB], uint32_t m, float tau, int form) {
+  const float2 tp = f2(tau, tau), tn = f2(-tau, -tau);
   if (form == 0) {
 #pragma unroll
     for (int i = 0; i < EB; ++i)
@@ -131,8 +141,8 @@ __device__ __forceinline__ void rot_tan(float2 (&v)[1 << EB], uint32_t m, float 
         for (int r = 0; r < (1 << EB); ++r)
           if (!((r >> i) & 1)) {
             const float2 a = v[r], b = v[r | (1 << i)];
-            v[r] = f2(fmaf(tau, b.y, a.x), fmaf(-tau, b.x, a.y));
-            v[r | (1 << i)] = f2(fmaf(tau, a.y, b.x), fmaf(-tau, a.x, b.y));
+            v[r] = __ffma2_rn(tp, b, a);
+            v[r | (1 << i)] = __ffma2_rn(tn, a, b);
           }
       }
   } else {
@@ -143,71 +153,42 @@ __device__ __forceinline__ void rot_tan(float2 (&v)[1 << EB], uint32_t m, float 
         for (int r = 0; r < (1 << EB); ++r)
           if (!((r >> i) & 1)) {
             const float2 a = v[r], b = v[r | (1 << i)];
-            v[r] = f2(fmaf(-tau, a.y, b.x), fmaf(tau, a.x, b.y));
-            v[r | (1 << i)] = f2(fmaf(-tau, b.y, a.x), fmaf(tau, b.x, a.y));
+            v[r] = __ffma2_rn(tp, a, b);
+            v[r | (1 << i)] = __ffma2_rn(tp, b, f2(-a.x, -a.y));
           }
       }
   }
 }
 
-// Reduced-form rotation of the tile bits held by the lane-index bits in lm:
-// the partner amplitude comes from lane ^ 2^b by a warp shuffle.  The gate is
-// symmetric in (a, b), so both lanes apply the same update to their own value.
-template <int N>
-__device__ __forceinline__ void rot_lanes(float2 (&v)[N], uint32_t lm, float tau, int form) {
-#pragma unroll
-  for (int b = 0; b < 5; ++b)
-    if ((lm >> b) & 1u) {
-#pragma unroll
-      for (int r = 0; r < N; ++r) {
-        const float px = __shfl_xor_sync(0xffffffffu, v[r].x, 1 << b);
-        const float py = __shfl_xor_sync(0xffffffffu, v[r].y, 1 << b);
-        v[r] = form == 0 ? f2(fmaf(tau, py, v[r].x), fmaf(-tau, px, v[r].y))
-                         : f2(fmaf(-tau, v[r].y, px), fmaf(tau, v[r].x, py));
-      }
-    }
-}
-
-// Adjoint: reduced-form un-rotation of psi (v) and lambda (w), adding the raw
-// Im <lambda| X_q |psi> of each pair first; the round's sum is weighted by wr
-// (the squared scale the stored vectors owe at this point).
-template <int EB, bool LANES>
-__device__ __forceinline__ void unrot_tan(float2 (&v)[1 << EB], float2 (&w)[1 << EB], uint32_t m,
-                                          uint32_t lm, float tau, int form, float wr, float &acc) {
-  if constexpr (!LANES) lm = 0u;
-  if ((m | lm) == 0u) return;
-  float racc = 0.f;
+// Adjoint: un-rotation of psi (v) and lambda (w), adding first the raw
+// Im <lambda| X_q |psi> of each pair, which in the twisted basis is
+// lambda_a . psi_b - lambda_b . psi_a (real dot products of the complex
+// components); the round's sum is weighted by wr (the squared scale the
+// stored vectors owe at this point).
+template <int EB>
+__device__ __forceinline__ void unrot_tw(float2 (&v)[1 << EB], float2 (&w)[1 << EB], uint32_t m,
+                                         float tau, int form, float wr, float &acc) {
+  if (m == 0u) return;
+  float2 pp = f2(0.f, 0.f), pm = f2(0.f, 0.f);
 #pragma unroll
   for (int i = 0; i < EB; ++i)
     if ((m >> i) & 1u) {
 #pragma unroll
       for (int r = 0; r < (1 << EB); ++r)
         if (!((r >> i) & 1)) {
-          const float2 pa = v[r], pb = v[r | (1 << i)], la = w[r], lb = w[r | (1 << i)];
-          racc += la.x * pb.y - la.y * pb.x + lb.x * pa.y - lb.y * pa.x;
+          pp = __ffma2_rn(w[r], v[r | (1 << i)], pp);
+          pm = __ffma2_rn(w[r | (1 << i)], v[r], pm);
         }
     }
-  if constexpr (LANES) {
-#pragma unroll
-  for (int b = 0; b < 5; ++b)
-    if ((lm >> b) & 1u) {
-      // each lane adds Im(conj(lambda_self) psi_partner): the pair's two terms
-      // come from its two lanes
-#pragma unroll
-      for (int r = 0; r < (1 << EB); ++r) {
-        const float px = __shfl_xor_sync(0xffffffffu, v[r].x, 1 << b);
-        const float py = __shfl_xor_sync(0xffffffffu, v[r].y, 1 << b);
-        racc += w[r].x * py - w[r].y * px;
-      }
-    }
-  }
-  acc = fmaf(racc, wr, acc);
-  rot_tan<EB>(v, m, tau, form);
-  rot_tan<EB>(w, m, tau, form);
-  if constexpr (LANES) {
-    rot_lanes<(1 << EB)>(v, lm, tau, form);
-    rot_lanes<(1 << EB)>(w, lm, tau, form);
-  }
+  acc = fmaf((pp.x + pp.y) - (pm.x + pm.y), wr, acc);
+  rot_tw<EB>(v, m, tau, form);
+  rot_tw<EB>(w, m, tau, form);
+}
+
+// z * i^k (k folds to a constant where the register index is one)
+__device__ __forceinline__ float2 ipow(float2 z, int k) {
+  k &= 3;
+  return k == 0 ? z : k == 1 ? f2(-z.y, z.x) : k == 2 ? f2(-z.x, -z.y) : f2(z.y, -z.x);
 }
 
 __device__ __forceinline__ uint32_t pdep_d(uint32_t v, uint32_t mask) {
@@ -226,6 +207,14 @@ template <class PL, int R>
 __device__ __forceinline__ uint32_t thr_tile() {
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   return pdep_d(lane, PL::lane(R)) | pdep_d(warp, PL::warp(R));
+}
+
+// Twist exponent base of this thread in round R of tile T: register r holds
+// global index x with popc(x) = twist_base + popc(r), tile offset and tile
+// number filling disjoint bits of x.
+template <class PL, int R>
+__device__ __forceinline__ int twist_base(uint64_t T) {
+  return __popc(thr_tile<PL, R>()) + __popcll(T);
 }
 
 // Registers <- shared tile in round-R layout (16-byte accesses when the
@@ -526,52 +515,58 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off + s * L.cost_bytes);
       float2 v[NREG];
       if (P.init_plus) {
+        // |+>^n in the twisted basis: amp (-i)^popc(x)
+        const int b0 = twist_base<PL, 0>(T);
 #pragma unroll
-        for (int r = 0; r < NREG; ++r) v[r] = f2(P.amp, 0.f);
+        for (int r = 0; r < NREG; ++r) v[r] = ipow(f2(P.amp, 0.f), -(b0 + popc_c(r)));
       } else {
         lds_round<PL, 0, SW>(v, buf);
+        if (P.twist_in) {
+          const float2 z = ipow(f2(1.f, 0.f), -twist_base<PL, 0>(T));
+#pragma unroll
+          for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), -popc_c(r));
+        }
       }
       constexpr bool final0 = H1 && H2;  // s2 walks back down to round 0
       if constexpr (H1) {
-        rot_tan<EB>(v, P.s1.m[0], P.tau1, P.form1);
-        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s1.lm[0], P.tau1, P.form1);
+        rot_tw<EB>(v, P.s1.m[0], P.tau1, P.form1);
         xp<PL, 0, 1, SW>(v, buf);
-        rot_tan<EB>(v, P.s1.m[1], P.tau1, P.form1);
-        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s1.lm[1], P.tau1, P.form1);
+        rot_tw<EB>(v, P.s1.m[1], P.tau1, P.form1);
         if constexpr (NR == 3) {
           xp<PL, 1, 2, SW>(v, buf);
-          rot_tan<EB>(v, P.s1.m[2], P.tau1, P.form1);
-        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s1.lm[2], P.tau1, P.form1);
+          rot_tw<EB>(v, P.s1.m[2], P.tau1, P.form1);
         }
         if constexpr (PH) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tab, P.scl_phase);
         if constexpr (H2) {
-          rot_tan<EB>(v, P.s2.m[NR - 1], P.tau2, P.form2);
-        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[NR - 1], P.tau2, P.form2);
+          rot_tw<EB>(v, P.s2.m[NR - 1], P.tau2, P.form2);
           if constexpr (NR == 3) {
             xp<PL, 2, 1, SW>(v, buf);
-            rot_tan<EB>(v, P.s2.m[1], P.tau2, P.form2);
-        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[1], P.tau2, P.form2);
+            rot_tw<EB>(v, P.s2.m[1], P.tau2, P.form2);
           }
           xp<PL, 1, 0, SW>(v, buf);
-          rot_tan<EB>(v, P.s2.m[0], P.tau2, P.form2);
-          if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
+          rot_tw<EB>(v, P.s2.m[0], P.tau2, P.form2);
         }
       } else {
         if constexpr (PH) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tab, P.scl_phase);
-        rot_tan<EB>(v, P.s2.m[0], P.tau2, P.form2);
-        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[0], P.tau2, P.form2);
+        rot_tw<EB>(v, P.s2.m[0], P.tau2, P.form2);
         xp<PL, 0, 1, SW>(v, buf);
-        rot_tan<EB>(v, P.s2.m[1], P.tau2, P.form2);
-        if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[1], P.tau2, P.form2);
+        rot_tw<EB>(v, P.s2.m[1], P.tau2, P.form2);
         if constexpr (NR == 3) {
           xp<PL, 1, 2, SW>(v, buf);
-          rot_tan<EB>(v, P.s2.m[2], P.tau2, P.form2);
-          if constexpr (SW == 64) rot_lanes<NREG>(v, P.s2.lm[2], P.tau2, P.form2);
+          rot_tw<EB>(v, P.s2.m[2], P.tau2, P.form2);
         }
       }
+      constexpr int RS = (H1 && H2) ? 0 : NR - 1;  // the round the tile is stored from
       if (P.end_scale) {
+        if (P.untwist) {
+          // back to the standard basis: psi(x) = i^popc(x) s(x)
+          const float2 z = cmulf(P.scl_end, ipow(f2(1.f, 0.f), twist_base<PL, RS>(T)));
 #pragma unroll
-        for (int r = 0; r < NREG; ++r) v[r] = cmulf(v[r], P.scl_end);
+          for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), popc_c(r));
+        } else {
+#pragma unroll
+          for (int r = 0; r < NREG; ++r) v[r] = cmulf(v[r], P.scl_end);
+        }
       }
       float e = 0.f, o = 0.f;
       if constexpr (final0) {
@@ -731,20 +726,20 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
         lds_round<PL, 0, SW>(w, bw);
       }
       float a1 = 0.f, ag = 0.f, a2 = 0.f;
-      unrot_tan<EB, SW == 64>(v, w, P.s1.m[0], P.s1.lm[0], P.tau1, P.form1, P.w1[0], a1);
+      unrot_tw<EB>(v, w, P.s1.m[0], P.tau1, P.form1, P.w1[0], a1);
       sts_round<PL, 0, SW>(v, bv);
       sts_round<PL, 0, SW>(w, bw);
       cbar();
       lds_round<PL, 1, SW>(v, bv);
       lds_round<PL, 1, SW>(w, bw);
-      unrot_tan<EB, SW == 64>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
+      unrot_tw<EB>(v, w, P.s1.m[1], P.tau1, P.form1, P.w1[1], a1);
       if constexpr (NR == 3) {
         sts_round<PL, 1, SW>(v, bv);
         sts_round<PL, 1, SW>(w, bw);
         cbar();
         lds_round<PL, 2, SW>(v, bv);
         lds_round<PL, 2, SW>(w, bw);
-        unrot_tan<EB, SW == 64>(v, w, P.s1.m[2], P.s1.lm[2], P.tau1, P.form1, P.w1[2], a1);
+        unrot_tw<EB>(v, w, P.s1.m[2], P.tau1, P.form1, P.w1[2], a1);
       }
       if constexpr (PH) {
         // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
@@ -762,21 +757,27 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       }
       constexpr bool final0 = H2;
       if constexpr (H2) {
-        unrot_tan<EB, SW == 64>(v, w, P.s2.m[NR - 1], P.s2.lm[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
+        unrot_tw<EB>(v, w, P.s2.m[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
         if constexpr (NR == 3) {
           sts_round<PL, 2, SW>(v, bv);
           sts_round<PL, 2, SW>(w, bw);
           cbar();
           lds_round<PL, 1, SW>(v, bv);
           lds_round<PL, 1, SW>(w, bw);
-          unrot_tan<EB, SW == 64>(v, w, P.s2.m[1], P.s2.lm[1], P.tau2, P.form2, P.w2[1], a2);
+          unrot_tw<EB>(v, w, P.s2.m[1], P.tau2, P.form2, P.w2[1], a2);
         }
         sts_round<PL, 1, SW>(v, bv);
         sts_round<PL, 1, SW>(w, bw);
         cbar();
         lds_round<PL, 0, SW>(v, bv);
         lds_round<PL, 0, SW>(w, bw);
-        unrot_tan<EB, SW == 64>(v, w, P.s2.m[0], P.s2.lm[0], P.tau2, P.form2, P.w2[0], a2);
+        unrot_tw<EB>(v, w, P.s2.m[0], P.tau2, P.form2, P.w2[0], a2);
+      }
+      if (P.untwist) {
+        // psi back to the standard basis (lambda is scratch from here on)
+        const float2 z = ipow(f2(1.f, 0.f), twist_base<PL, final0 ? 0 : NR - 1>(T));
+#pragma unroll
+        for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), popc_c(r));
       }
       if constexpr (final0) {
         sts_round<PL, 0, SW>(v, bv);
