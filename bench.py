@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--cpu-sample-n", type=int, default=22,
                     help="n of the oracle sample timed for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None,
+                    help="LABS size override (a smaller case for profiling; default n=30)")
+    ap.add_argument("--p", type=int, default=None,
+                    help="layer-count override (default p=10)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=400)
     return ap.parse_args()
@@ -143,21 +147,34 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def traffic_record(kind):
-    """DRAM bytes per launch of `kind` from the committed ncu summary, or
-    None when the kernel source changed since the capture."""
+KERNEL_SOURCES = ("tma_kernels.cu", "kernels.h", "qaoa_common.cuh")
+
+
+def kernel_source_hash():
+    """sha256 (16 hex digits) over the sources of the tiled TMA kernels."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2309_04841_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kind, n, p):
+    """Mean DRAM bytes per launch of `kind` on this workload from the
+    committed ncu summary, or None when the kernel sources changed since the
+    capture or the summary covers another workload."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_2309_04841_gb300", "csrc", "pass_kernels.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha256_16") != h:
+    if rec.get("source_sha256_16") != kernel_source_hash():
+        return None
+    if rec.get("n") != n or rec.get("p") != p:
         return None
     k = rec.get("kernels", {}).get(kind)
-    return None if k is None else k.get("dram_bytes_per_launch_full_size")
+    return None if k is None else k.get("dram_bytes_per_launch")
 
 
 def cpu_baseline(sample_n, p, n_full):
@@ -181,6 +198,16 @@ def cpu_baseline(sample_n, p, n_full):
             "sample_seconds": dt}
 
 
+def bench_workload(a):
+    from paper_2309_04841_gb300 import inputs as I
+    w = I.workload(WORKLOAD, n=a.n)
+    if a.p is not None:
+        w["p"] = a.p
+    if a.n is not None or a.p is not None:
+        w["name"] = f"labs{w['n']}_p{w['p']}"
+    return w
+
+
 # --------------------------------------------------------------- our arm
 
 def run_ours(a, ws, rank, local):
@@ -192,7 +219,7 @@ def run_ours(a, ws, rank, local):
 
     torch.cuda.set_device(local)
     Q.lib()
-    w = I.workload(WORKLOAD)
+    w = bench_workload(a)
     n, p = w["n"], w["p"]
     N = 1 << n
     g, b = I.workload_angles(w)
@@ -267,7 +294,7 @@ def run_ours(a, ws, rank, local):
     per_launch_bytes = d["bytes"] / d["launches"]
     per_launch_ms = d["ms"] / d["launches"]
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-    traffic = traffic_record(dom)
+    traffic = traffic_record(dom, n, p)
     launches = sum(v["launches"] for v in kinds.values())
     step_bytes = (20.0 * p + 36.0 * p) * N  # forward + adjoint layers (algorithmic)
     step_alg = step_bytes * value / ws / 1e9
@@ -276,10 +303,10 @@ def run_ours(a, ws, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"LABS n={n} p={p} objective+gradient ({WORKLOAD})",
+        "config": {"workload": f"LABS n={n} p={p} objective+gradient ({w['name']})",
                    "n": n, "p": p, "state": "complex64", "cost": "int32",
                    "angles": "gamma, beta ~ U[0, pi) seeds 6 / 16",
-                   "l2": "inputs larger than L2 (8 GiB state, 4 GiB cost vector)",
+                   "l2": f"inputs larger than L2 ({8 * N / 2**30:g} GiB state, {4 * N / 2**30:g} GiB cost vector)",
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": a.steps * ws / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * p * 8, "d2h_bytes_per_step": (2 + 2 * p) * 8},
@@ -387,8 +414,7 @@ def run_reference(a, ws, rank):
     (obj+grad at n = cpu_sample_n), expressed in n = 30 evals/s."""
     if rank != 0:
         return None
-    from paper_2309_04841_gb300 import inputs as I
-    w = I.workload(WORKLOAD)
+    w = bench_workload(a)
     for _ in range(a.warmup):
         cpu_baseline(min(a.cpu_sample_n, 16), w["p"], w["n"])
     vals, secs = [], []
@@ -402,7 +428,7 @@ def run_reference(a, ws, rank):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"LABS n={w['n']} p={w['p']} objective+gradient ({WORKLOAD})",
+            "config": {"workload": f"LABS n={w['n']} p={w['p']} objective+gradient ({w['name']})",
                        "n": w["n"], "p": w["p"]},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -520,6 +520,16 @@ bool tma_ok(qaoa_cost_type ct) { return ct == QAOA_COST_I32 || ct == QAOA_COST_F
 
 // Reduced ("tan") form of exp(-i b X) (forward) or exp(+i b X) (adjoint):
 // exp(-/+ i b X) = sigma * G with |tau| <= 1 (see TmaFwdParams).
+// f_min as the 32-bit word the cost vector holds (int32 or float32 bits).
+uint32_t fmin_word(qaoa_cost_type ct, const qaoa_cost_stats *stats) {
+  const double f = stats ? stats->f_min : 0.0;
+  if (ct == QAOA_COST_I32) return (uint32_t)(int32_t)f;
+  const float x = (float)f;
+  uint32_t w;
+  memcpy(&w, &x, sizeof(w));
+  return w;
+}
+
 struct TanRot {
   float tau;
   int form;
@@ -608,7 +618,7 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
     P.twist_in = &op == &ops.front() && !op.init;
     P.amp = (float)(1.0 / sqrt(ldexp(1.0, n)));
     P.reduce = op.reduce;
-    P.fmin_d = stats ? stats->f_min : 0.0;
+    P.fmin_word = fmin_word(ct, stats);
     P.partials = ws.partials;
     P.counter = ws.counter;
     P.out = d_out;

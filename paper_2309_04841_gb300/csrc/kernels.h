@@ -107,7 +107,7 @@ struct alignas(64) TmaFwdParams {
   int twist_in;  // first pass on a caller's state: into the twisted basis
   int untwist;   // last pass (with end_scale): back to the standard basis
   float amp;
-  double fmin_d;
+  uint32_t fmin_word;  // f_min as the cost vector stores it (int32 or float32 bits)
   double *partials;
   unsigned *counter;
   double *out;

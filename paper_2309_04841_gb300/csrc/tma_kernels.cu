@@ -314,9 +314,23 @@ __device__ __forceinline__ void phase_round(float2 (&v)[PL::NREG], const uint32_
   }
 }
 
+// Float-float running sum (Knuth's TwoSum adds each term exactly into hi + lo):
+// per-thread tile sums stay off the FP64 pipe, which is narrow on this part.
+struct FF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = hi + x, bb = s - hi;
+    lo += (hi - (s - bb)) + (x - bb);
+    hi = s;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 template <class PL, int R>
 __device__ __forceinline__ void eo_round(const float2 (&v)[PL::NREG], const uint32_t *cb, int kind,
-                                         double fmin, float &e, float &o) {
+                                         uint32_t fmin_word, float &e, float &o) {
+  // f == f_min is tested on the raw 32-bit words (exact for int32 costs; for
+  // float32 costs f_min is one of the stored values, and +0 / -0 compare equal)
   const uint32_t tt = thr_tile<PL, R>();
 #pragma unroll
   for (int r = 0; r < PL::NREG; ++r) {
@@ -324,7 +338,8 @@ __device__ __forceinline__ void eo_round(const float2 (&v)[PL::NREG], const uint
     const float f = cost_val(kind, w);
     const float pr = v[r].x * v[r].x + v[r].y * v[r].y;
     e += pr * f;
-    o += ((double)f == fmin) ? pr : 0.f;
+    const bool at_min = kind == kCostI32 ? w == fmin_word : f == __uint_as_float(fmin_word);
+    o += at_min ? pr : 0.f;
   }
 }
 
@@ -498,7 +513,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     }
   } else {
     // ---------------- compute warps
-    double acc_e = 0.0, acc_o = 0.0;  // this thread's energy / overlap terms
+    FF acc_e, acc_o;  // this thread's energy / overlap terms
     for (int i = 0;; ++i) {
       const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
       if (T >= P.ntiles) break;
@@ -570,10 +585,10 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       }
       float e = 0.f, o = 0.f;
       if constexpr (final0) {
-        if constexpr (RED) eo_round<PL, 0>(v, cb, P.cost_kind, P.fmin_d, e, o);
+        if constexpr (RED) eo_round<PL, 0>(v, cb, P.cost_kind, P.fmin_word, e, o);
         sts_round<PL, 0, SW>(v, buf);
       } else {
-        if constexpr (RED) eo_round<PL, NR - 1>(v, cb, P.cost_kind, P.fmin_d, e, o);
+        if constexpr (RED) eo_round<PL, NR - 1>(v, cb, P.cost_kind, P.fmin_word, e, o);
         sts_round<PL, NR - 1, SW>(v, buf);
       }
       fence_async_smem();
@@ -593,13 +608,13 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
         }
       }
       if constexpr (RED) {
-        acc_e += (double)e;
-        acc_o += (double)o;
+        acc_e.add(e);
+        acc_o.add(o);
       }
     }
     if (NS == 1 && tid == 0) bulk_wait0();
     if constexpr (RED) {
-      double a[2] = {acc_e, acc_o};
+      double a[2] = {acc_e.value(), acc_o.value()};
       csum<2>(a, red);
       if (tid == 0) {
         P.partials[blockIdx.x * 2] = a[0];
@@ -696,7 +711,7 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       bulk_wait0();
     }
   } else {
-    double acc1 = 0.0, accg = 0.0, acc2 = 0.0;  // this thread's gradient terms
+    FF acc1, accg, acc2;  // this thread's gradient terms
     for (int i = 0;; ++i) {
       const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
       if (T >= P.ntiles) break;
@@ -800,12 +815,12 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
           }
         }
       }
-      acc1 += (double)a1;
-      accg += (double)ag;
-      acc2 += (double)a2;
+      acc1.add(a1);
+      accg.add(ag);
+      acc2.add(a2);
     }
     if (NS == 1 && tid == 0) bulk_wait0();
-    double a[3] = {acc1, accg, acc2};
+    double a[3] = {acc1.value(), accg.value(), acc2.value()};
     csum<3>(a, red);
     if (tid == 0) {
       P.partials[blockIdx.x * 3] = a[0];
