@@ -198,6 +198,19 @@ def cpu_baseline(sample_n, p, n_full):
             "sample_seconds": dt}
 
 
+def group_kinds(kinds, steps):
+    """Per-kind profile entries ("bwd_high.k6") summed by pass group ("bwd_high")."""
+    g = {}
+    for k, v in kinds.items():
+        e = g.setdefault(k.split(".")[0], {"launches": 0, "ms": 0.0, "bytes": 0.0})
+        e["launches"] += v["launches"]
+        e["ms"] += v["ms"]
+        e["bytes"] += v["bytes"]
+    return {k: {"launches": e["launches"], "ms_per_step": e["ms"] / steps,
+                "GBps": e["bytes"] / (e["ms"] * 1e-3) / 1e9 if e["ms"] > 0 else None}
+            for k, e in g.items()}
+
+
 def bench_workload(a):
     from paper_2309_04841_gb300 import inputs as I
     w = I.workload(WORKLOAD, n=a.n)
@@ -316,6 +329,7 @@ def run_ours(a, ws, rank, local):
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s"},
         "step_roofline": {"algorithmic_bytes_per_step": step_bytes,
                           "achieved_GBps": step_alg, "frac": step_alg / peak},
+        "kernel_groups": group_kinds(kinds, a.steps),
         "kernels": {k: {"launches": v["launches"], "ms_per_step": v["ms"] / a.steps,
                         "GBps": (v["bytes"] / v["launches"]) / ((v["ms"] / v["launches"]) * 1e-3) / 1e9
                         if v["ms"] > 0 else None} for k, v in kinds.items()},

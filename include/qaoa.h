@@ -72,9 +72,13 @@ typedef struct {
 
 /* Statistics of a cost vector that later calls need. */
 typedef struct {
-    double f_min;    /* min_x f[x]                                   */
-    double f_max;    /* max_x f[x]                                   */
-    uint64_t n_min;  /* number of x with f[x] == f_min (ground states) */
+    double f_min;       /* min_x f[x]                                    */
+    double f_max;       /* max_x f[x]                                    */
+    uint64_t n_min;     /* number of x with f[x] == f_min (ground states) */
+    uint32_t step_log2; /* int32 costs: largest k with 2^k dividing every
+                           f[x] - f_min (LABS: 2); 0 for other cost types
+                           and for a constant vector.  0 is always valid. */
+    uint32_t reserved;  /* 0 */
 } qaoa_cost_stats;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -147,9 +151,11 @@ qaoa_status qaoa_maxcut_costs(int n, const int32_t *edges, const double *w,
                               qaoa_stream_t stream);
 
 /*
- * Minimum, maximum and number of minimisers of a cost vector.  d_work is a
- * device workspace of at least qaoa_workspace_bytes(n) bytes.  Writes the
- * result to *h_out (host).  Synchronises `stream`.
+ * Minimum, maximum and number of minimisers of a cost vector, and for int32
+ * costs the largest power of two dividing every f[x] - f_min (the phase
+ * tables of later calls index (f - f_min) >> step_log2).  d_work is a device
+ * workspace of at least qaoa_workspace_bytes(n) bytes.  Writes the result to
+ * *h_out (host).  Synchronises `stream`.
  */
 qaoa_status qaoa_cost_stats_compute(int n, const void *d_costs,
                                     qaoa_cost_type ct, void *d_work,
@@ -179,7 +185,9 @@ qaoa_status qaoa_workspace_check(void *d_work, size_t work_bytes, qaoa_stream_t 
 /*
  * Algorithm 3: p layers of  psi <- exp(-i beta_l sum X) exp(-i gamma_l f) psi.
  *   d_costs/ct: the cost vector; stats: from qaoa_cost_stats_compute on it
- *     (host struct; only f_min/f_max are read).
+ *     (host struct; f_min, f_max and step_log2 are read; a struct filled by
+ *     hand must satisfy f_min <= f[x] <= f_max, and step_log2 = 0 is always
+ *     valid).
  *   gammas, betas: host arrays of p finite doubles, 1 <= p <= 100000.
  *   d_state: device, 2^n amplitudes of type st, updated in place.  If
  *     init_plus != 0 the input is ignored and the simulation starts from

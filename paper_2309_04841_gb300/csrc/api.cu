@@ -53,6 +53,32 @@ qaoa_status cuda_fail(cudaError_t e, const char *where) {
     if (_e != cudaSuccess) return cuda_fail(_e, kind " launch"); \
   } while (0)
 
+// The same with a run-time label (static storage).
+#define LAUNCH_N(name, bytes, st, call)                       \
+  do {                                                        \
+    const int _pid = prof_begin(st);                          \
+    cudaError_t _e = (call);                                  \
+    prof_end(_pid, st, name, (double)(bytes));                \
+    if (_e != cudaSuccess) return cuda_fail(_e, "TMA pass launch"); \
+  } while (0)
+
+// Profile label of a TMA pass: "fwd_high.k7" etc.  Kind bits: forward 1 =
+// first sweep, 2 = phase, 4 = second sweep, 8 = energy / overlap; adjoint (the
+// first un-mix sweep is always there) 2 = d/d gamma + un-phase, 4 = second
+// un-mix sweep, 8 = lambda = f psi.
+const char *tma_pass_name(bool fwd, bool high, int k) {
+  static char names[2][2][16][24];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    for (int f = 0; f < 2; ++f)
+      for (int h = 0; h < 2; ++h)
+        for (int j = 0; j < 16; ++j)
+          snprintf(names[f][h][j], sizeof(names[f][h][j]), "%s_%s.k%d", f ? "fwd" : "bwd",
+                   h ? "high" : "low", j);
+  });
+  return names[fwd ? 1 : 0][high ? 1 : 0][k & 15];
+}
+
 int num_sms() {
   static int cache[64] = {0};
   int dev = 0;
@@ -80,7 +106,7 @@ constexpr size_t kWsCounters = 0, kWsSmall = 256, kWsPartials = 512;
 size_t partial_doubles(int n) {
   const size_t tiles = n > 11 ? ((size_t)1 << (n - 11)) : 1;  // smallest tile: 2^11
   size_t need = tiles * 3;
-  const size_t red = (size_t)1024 * 3;  // cost-stats / expectation grids
+  const size_t red = (size_t)1024 * 4;  // cost-stats / expectation grids
   return need > red ? need : red;
 }
 
@@ -145,16 +171,37 @@ void make_phase(PhaseDigits &ph, double g, qaoa_cost_type ct, const qaoa_cost_st
                 std::complex<double> scale) {
   memset(&ph, 0, sizeof(ph));
   const double range = stats ? stats->f_max - stats->f_min : 1e300;
-  if (ct == QAOA_COST_I32 && stats && range >= 0 && range < 32768.0) {
+  const int shift = stats && stats->step_log2 < 31 ? (int)stats->step_log2 : 0;
+  const double rr = range >= 0 ? std::floor(range / std::ldexp(1.0, shift)) : -1.0;  // max d
+  auto put = [&](int e, double angle, bool last) {
+    std::complex<double> z(cos(angle), -sin(angle));
+    if (last) z *= scale;
+    ph.d[e] = make_float2((float)z.real(), (float)z.imag());
+  };
+  const double fmin = stats ? stats->f_min : 0.0, unit = std::ldexp(g, shift);
+  if (ct == QAOA_COST_I32 && stats && rr >= 0 && 64.0 + std::floor(rr / 64.0) + 1.0 <= kPhaseMaxEntries) {
+    // two digits: D0[d & 63], D1[d >> 6] (D1 with exp(-i g fmin) and the scale)
+    const int n1 = (int)std::floor(rr / 64.0) + 1;
     ph.mode = 0;
-    ph.fmin = (int)stats->f_min;
+    ph.nd = 2;
+    ph.fmin = (int)fmin;
+    ph.shift = shift;
+    ph.last = n1 - 1;
+    ph.nent = 64 + n1;
+    for (int j = 0; j < 64; ++j) put(j, unit * j, false);
+    for (int j = 0; j < n1; ++j) put(64 + j, g * fmin + unit * 64.0 * j, true);
+  } else if (ct == QAOA_COST_I32 && stats && rr >= 0 && rr < 32768.0) {
+    // three 5-bit digits
+    ph.mode = 0;
+    ph.nd = 3;
+    ph.fmin = (int)fmin;
+    ph.shift = shift;
+    ph.last = 31;
+    ph.nent = 96;
     for (int j = 0; j < 32; ++j) {
-      const double a0 = g * (double)j, a1 = g * (double)(32 * j);
-      const double a2 = g * ((double)stats->f_min + 1024.0 * (double)j);
-      const std::complex<double> z2 = std::complex<double>(cos(a2), -sin(a2)) * scale;
-      ph.d[0][j] = make_float2((float)cos(a0), (float)-sin(a0));
-      ph.d[1][j] = make_float2((float)cos(a1), (float)-sin(a1));
-      ph.d[2][j] = make_float2((float)z2.real(), (float)z2.imag());
+      put(j, unit * j, false);
+      put(32 + j, unit * 32.0 * j, false);
+      put(64 + j, g * fmin + unit * 1024.0 * j, true);
     }
   } else {
     ph.mode = 1;
@@ -625,10 +672,8 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
     P.err = ws.err;
     const double N = (double)(1ull << n);
     const double bytes = (P.init_plus ? 8.0 : 16.0) * N + ((P.has_phase || P.reduce) ? 4.0 * N : 0.0);
-    if (G.high)
-      LAUNCH("fwd_high", bytes, s, launch_fwd_tma(P, true, s, nsm));
-    else
-      LAUNCH("fwd_low", bytes, s, launch_fwd_tma(P, false, s, nsm));
+    const int kind = (op.l1 >= 0 ? 1 : 0) | (P.has_phase ? 2 : 0) | (op.l2 >= 0 ? 4 : 0) | (P.reduce ? 8 : 0);
+    LAUNCH_N(tma_pass_name(true, G.high, kind), bytes, s, launch_fwd_tma(P, G.high, s, nsm));
   }
   return QAOA_OK;
 }
@@ -702,10 +747,8 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     P.err = ws.err;
     const double N = (double)(1ull << n);
     const double bytes = (P.init_lambda ? 24.0 : 32.0) * N + ((P.has_phase || P.init_lambda) ? 4.0 * N : 0.0);
-    if (G.high)
-      LAUNCH("bwd_high", bytes, s, launch_bwd_tma(P, true, s, nsm));
-    else
-      LAUNCH("bwd_low", bytes, s, launch_bwd_tma(P, false, s, nsm));
+    const int kind = (P.has_phase ? 2 : 0) | (op.l2 >= 0 ? 4 : 0) | (P.init_lambda ? 8 : 0);
+    LAUNCH_N(tma_pass_name(false, G.high, kind), bytes, s, launch_bwd_tma(P, G.high, s, nsm));
   }
   return QAOA_OK;
 }
@@ -973,12 +1016,15 @@ qaoa_status qaoa_cost_stats_compute(int n, const void *d_costs, qaoa_cost_type c
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
   LAUNCH("cost_stats", cost_bytes(ct) * (double)(1ull << n), s,
          launch_cost_stats(n, d_costs, cost_kind(ct), ws.partials, ws.counter, ws.small, s, num_sms()));
-  double h[3];
+  double h[4];
   CK(cudaMemcpyAsync(h, ws.small, sizeof(h), cudaMemcpyDeviceToHost, s), "cost stats copy");
   CK(cudaStreamSynchronize(s), "cost stats sync");
   h_out->f_min = h[0];
   h_out->f_max = h[1];
   h_out->n_min = (uint64_t)h[2];
+  const uint32_t bits = (uint32_t)h[3];
+  h_out->step_log2 = bits ? (uint32_t)__builtin_ctz(bits) : 0u;
+  h_out->reserved = 0u;
   return QAOA_OK;
 }
 

@@ -129,16 +129,22 @@ __device__ __forceinline__ MinMaxCnt mmc_join(MinMaxCnt a, MinMaxCnt b) {
 }
 
 // Fixed-shape grid-stride reduction; per-block partials; the last block
-// merges them in block order.  out: [f_min, f_max, n_min].
+// merges them in block order.  out: [f_min, f_max, n_min, step bits], where
+// step bits = OR over x of (f[x] - f[0]) for int32 costs (0 otherwise): its
+// lowest set bit is the largest power of two dividing every f[x] - f_min.
 __global__ void __launch_bounds__(256) k_cost_stats(int n, const void *cost, int kind,
                                                    double *partials, unsigned *counter,
                                                    double *out) {
   const uint64_t N = 1ull << n;
   MinMaxCnt a = {INFINITY, -INFINITY, 0.0};
+  uint32_t bits = 0u;
+  const int *ci = reinterpret_cast<const int *>(cost);
+  const int f0 = kind == kCostI32 ? __ldg(ci) : 0;
   for (uint64_t x = blockIdx.x * 256ull + threadIdx.x; x < N; x += (uint64_t)gridDim.x * 256ull) {
     const double f = cost_at(cost, kind, x);
     MinMaxCnt b = {f, f, 1.0};
     a = mmc_join(a, b);
+    if (kind == kCostI32) bits |= (uint32_t)(__ldg(ci + x) - f0);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -147,17 +153,27 @@ __global__ void __launch_bounds__(256) k_cost_stats(int n, const void *cost, int
     b.mx = __shfl_down_sync(0xffffffffu, a.mx, o);
     b.cnt = __shfl_down_sync(0xffffffffu, a.cnt, o);
     a = mmc_join(a, b);
+    bits |= __shfl_down_sync(0xffffffffu, bits, o);
   }
   __shared__ MinMaxCnt sw[8];
+  __shared__ uint32_t sb[8];
   __shared__ int am_last;
-  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = a;
+  if ((threadIdx.x & 31) == 0) {
+    sw[threadIdx.x >> 5] = a;
+    sb[threadIdx.x >> 5] = bits;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     MinMaxCnt r = sw[0];
-    for (int i = 1; i < 8; ++i) r = mmc_join(r, sw[i]);
-    partials[blockIdx.x * 3 + 0] = r.mn;
-    partials[blockIdx.x * 3 + 1] = r.mx;
-    partials[blockIdx.x * 3 + 2] = r.cnt;
+    uint32_t rb = sb[0];
+    for (int i = 1; i < 8; ++i) {
+      r = mmc_join(r, sw[i]);
+      rb |= sb[i];
+    }
+    partials[blockIdx.x * 4 + 0] = r.mn;
+    partials[blockIdx.x * 4 + 1] = r.mx;
+    partials[blockIdx.x * 4 + 2] = r.cnt;
+    partials[blockIdx.x * 4 + 3] = (double)rb;
     __threadfence();
     am_last = (atomicAdd(counter, 1u) == gridDim.x - 1u);
   }
@@ -165,13 +181,16 @@ __global__ void __launch_bounds__(256) k_cost_stats(int n, const void *cost, int
   if (am_last && threadIdx.x == 0) {
     __threadfence();
     MinMaxCnt r = {INFINITY, -INFINITY, 0.0};
+    uint32_t rb = 0u;
     for (unsigned b = 0; b < gridDim.x; ++b) {
-      MinMaxCnt q = {__ldcg(partials + b * 3), __ldcg(partials + b * 3 + 1), __ldcg(partials + b * 3 + 2)};
+      MinMaxCnt q = {__ldcg(partials + b * 4), __ldcg(partials + b * 4 + 1), __ldcg(partials + b * 4 + 2)};
       r = mmc_join(r, q);
+      rb |= (uint32_t)__ldcg(partials + b * 4 + 3);
     }
     out[0] = r.mn;
     out[1] = r.mx;
     out[2] = r.cnt;
+    out[3] = (double)rb;
     *counter = 0u;
   }
 }

@@ -76,22 +76,29 @@ static_assert(PlanTmaB12Low::valid() && PlanTmaB12High::valid(), "bad TMA B12 pl
 // sigmas and folds it into the next phase multiply (scl_phase, or the phase
 // table) or applies it at the end of the pass (scl_end).
 
-// Phase factors of the TMA passes.  Mode 0 (integer costs, f_max - f_min <
-// 2^15): with d = f - fmin split into three 5-bit digits,
-//   exp(-i g f) = D0[d & 31] * D1[(d >> 5) & 31] * D2[d >> 10],
-// D2 also carrying exp(-i g fmin) and the pending scale.  Shared memory holds
-// each table as 16 interleaved copies, so the 16 lanes of a half-warp read 16
-// different bank pairs whatever their costs.  Mode 1: computed from g / 2pi =
-// g_hi + g_lo (float-float).
+// Phase factors of the TMA passes.  Mode 0 (integer costs): with
+// d = (f - fmin) >> shift (every f - fmin a multiple of 2^shift),
+//   nd = 2:  exp(-i g f) = D0[d & 63] * D1[d >> 6],
+//   nd = 3:  exp(-i g f) = D0[d & 31] * D1[(d >> 5) & 31] * D2[d >> 10],
+// the last table also carrying exp(-i g fmin) and the pending scale; the
+// tables lie back to back in d[] (nent entries).  Shared memory holds each
+// entry as 16 interleaved copies, so the 16 lanes of a half-warp read 16
+// different bank pairs whatever their costs.  Mode 1: computed from
+// g / 2pi = g_hi + g_lo (float-float).
+constexpr int kPhaseCopies = 16;
+constexpr int kPhaseMaxEntries = 112;
+constexpr int kPhaseTabEntries = kPhaseMaxEntries * kPhaseCopies;
+
 struct PhaseDigits {
   int mode;
   int fmin;
+  int shift;
+  int nd;     // 2 or 3 digits
+  int last;   // entries of the last table - 1 (its index is clamped to this)
+  int nent;   // entries in use
   float g_hi, g_lo;
-  float2 d[3][32];
+  float2 d[kPhaseMaxEntries];
 };
-
-constexpr int kPhaseCopies = 16;
-constexpr int kPhaseTabEntries = 3 * 32 * kPhaseCopies;
 
 struct alignas(64) TmaFwdParams {
   CUtensorMap map_psi;   // state, 8-byte elements, 128-byte swizzle

@@ -257,40 +257,57 @@ __device__ __forceinline__ void xp(float2 (&v)[PL::NREG], float2 *buf) {
 }
 
 // exp(-i g f) from the raw 32-bit cost word (int32 or float32).
+// exp(-i g f) from the raw 32-bit cost word; M = 2 / 3: digit tables with M
+// digits (integer costs), M = 1: computed (int32 or float32 costs).  Callers
+// branch on the mode once per round, outside their register loops.
+template <int M>
 __device__ __forceinline__ float2 phase_of(const PhaseDigits &ph, int kind, const float2 *tab,
                                            uint32_t word) {
-  if (ph.mode == 0) {
-    // three conflict-free lookups: this lane's copy of each digit table
-    const uint32_t d = (uint32_t)((int)word - ph.fmin);
+  if constexpr (M == 2 || M == 3) {
+    // conflict-free lookups: this lane's copy of each digit table
+    const uint32_t d = (uint32_t)((int)word - ph.fmin) >> ph.shift;
     const uint32_t q = threadIdx.x & (kPhaseCopies - 1);
-    const float2 a = tab[((d & 31u) << 4) | q];
-    const float2 b = tab[((32u + ((d >> 5) & 31u)) << 4) | q];
-    const float2 c = tab[((64u + min(d >> 10, 31u)) << 4) | q];
-    return cmulf(cmulf(a, b), c);
-  }
-  float fh, fl;
-  if (kind == kCostI32) {
-    const int f = (int)word;
-    fh = (float)f;
-    fl = (float)((long long)f - (long long)fh);
+    if constexpr (M == 2) {
+      const float2 a = tab[((d & 63u) << 4) | q];
+      const float2 b = tab[((64u + min(d >> 6, (uint32_t)ph.last)) << 4) | q];
+      return cmulf(a, b);
+    } else {
+      const float2 a = tab[((d & 31u) << 4) | q];
+      const float2 b = tab[((32u + ((d >> 5) & 31u)) << 4) | q];
+      const float2 c = tab[((64u + min(d >> 10, (uint32_t)ph.last)) << 4) | q];
+      return cmulf(cmulf(a, b), c);
+    }
   } else {
-    fh = __uint_as_float(word);
-    fl = 0.f;
+    float fh, fl;
+    if (kind == kCostI32) {
+      const int f = (int)word;
+      fh = (float)f;
+      fl = (float)((long long)f - (long long)fh);
+    } else {
+      fh = __uint_as_float(word);
+      fl = 0.f;
+    }
+    // g f / 2pi as a float-float: Dekker's two-product p + e = g_hi * fh via fma
+    const float p = ph.g_hi * fh;
+    const float e = fmaf(ph.g_hi, fh, -p);
+    const float r = (p - rintf(p)) + (e + fmaf(ph.g_hi, fl, ph.g_lo * fh));
+    float sn, cs;
+    sincospif(2.0f * r, &sn, &cs);
+    return f2(cs, -sn);
   }
-  // g f / 2pi as a float-float: Dekker's two-product p + e = g_hi * fh via fma
-  const float p = ph.g_hi * fh;
-  const float e = fmaf(ph.g_hi, fh, -p);
-  const float r = (p - rintf(p)) + (e + fmaf(ph.g_hi, fl, ph.g_lo * fh));
-  float sn, cs;
-  sincospif(2.0f * r, &sn, &cs);
-  return f2(cs, -sn);
 }
 
-// Shared-memory copy of the digit tables: entry j of table k, copy q at
-// ((32 k + j) * 16 + q).
+// Phase mode of a pass as the template argument of phase_of.
+__device__ __forceinline__ int phase_m(const PhaseDigits &ph) {
+  return ph.mode != 0 ? 1 : ph.nd == 2 ? 2 : 3;
+}
+
+// Shared-memory copy of the digit tables: entry e (of the concatenated
+// tables), copy q at e * 16 + q.
 template <int NT>
 __device__ __forceinline__ void fill_phase_tab(float2 *tab, const PhaseDigits &ph) {
-  for (int i = threadIdx.x; i < kPhaseTabEntries; i += NT) tab[i] = ph.d[i >> 9][(i >> 4) & 31];
+  const int n = min(ph.nent, kPhaseMaxEntries) * kPhaseCopies;
+  for (int i = threadIdx.x; i < n; i += NT) tab[i] = ph.d[i >> 4];
 }
 
 __device__ __forceinline__ float cost_val(int kind, uint32_t word) {
@@ -298,20 +315,29 @@ __device__ __forceinline__ float cost_val(int kind, uint32_t word) {
 }
 
 // v <- v * exp(-i g f) (* scl in computed mode; table mode has it folded in).
+template <class PL, int R, int M>
+__device__ __forceinline__ void phase_round_m(float2 (&v)[PL::NREG], const uint32_t *cb,
+                                              const PhaseDigits &ph, int kind, const float2 *tab,
+                                              float2 scl) {
+  const uint32_t tt = thr_tile<PL, R>();
+#pragma unroll
+  for (int r = 0; r < PL::NREG; ++r) {
+    const float2 z = phase_of<M>(ph, kind, tab, cb[tt | pdep(r, PL::reg(R))]);
+    v[r] = cmulf(v[r], M == 1 ? cmulf(scl, z) : z);
+  }
+}
+
 template <class PL, int R>
 __device__ __forceinline__ void phase_round(float2 (&v)[PL::NREG], const uint32_t *cb,
                                             const PhaseDigits &ph, int kind, const float2 *tab,
                                             float2 scl) {
-  const uint32_t tt = thr_tile<PL, R>();
-  if (ph.mode == 0) {
-#pragma unroll
-    for (int r = 0; r < PL::NREG; ++r)
-      v[r] = cmulf(v[r], phase_of(ph, kind, tab, cb[tt | pdep(r, PL::reg(R))]));
-  } else {
-#pragma unroll
-    for (int r = 0; r < PL::NREG; ++r)
-      v[r] = cmulf(v[r], cmulf(scl, phase_of(ph, kind, tab, cb[tt | pdep(r, PL::reg(R))])));
-  }
+  const int m = phase_m(ph);
+  if (m == 2)
+    phase_round_m<PL, R, 2>(v, cb, ph, kind, tab, scl);
+  else if (m == 3)
+    phase_round_m<PL, R, 3>(v, cb, ph, kind, tab, scl);
+  else
+    phase_round_m<PL, R, 1>(v, cb, ph, kind, tab, scl);
 }
 
 // Float-float running sum (Knuth's TwoSum adds each term exactly into hi + lo):
@@ -633,6 +659,25 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
 
 // ------------------------------------------------------------- adjoint
 
+// d/d gamma term Im <lambda| f |psi> of the round's amplitudes, then psi and
+// lambda times the un-phase factor exp(+i g f) (phase mode M as in phase_of).
+template <class PL, int R, int M>
+__device__ __forceinline__ void unphase_round(float2 (&v)[PL::NREG], float2 (&w)[PL::NREG],
+                                              const uint32_t *cb, const TmaBwdParams &P,
+                                              const float2 *tab, float &ag) {
+  const uint32_t tt = thr_tile<PL, R>();
+#pragma unroll
+  for (int r = 0; r < PL::NREG; ++r) {
+    const uint32_t word = cb[tt | pdep(r, PL::reg(R))];
+    const float f = cost_val(P.cost_kind, word);
+    ag += P.wg * f * (w[r].x * v[r].y - w[r].y * v[r].x);
+    float2 ph = phase_of<M>(P.ph, P.cost_kind, tab, word);
+    if constexpr (M == 1) ph = cmulf(ph, P.scl_phase);
+    v[r] = cmulf(v[r], ph);
+    w[r] = cmulf(w[r], ph);
+  }
+}
+
 template <class PL, int NS, int SW, int K>
 __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
@@ -758,17 +803,13 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
       }
       if constexpr (PH) {
         // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
-        const uint32_t tt = thr_tile<PL, NR - 1>();
-#pragma unroll
-        for (int r = 0; r < NREG; ++r) {
-          const uint32_t word = cb[tt | pdep(r, PL::reg(NR - 1))];
-          const float f = cost_val(P.cost_kind, word);
-          ag += P.wg * f * (w[r].x * v[r].y - w[r].y * v[r].x);
-          float2 ph = phase_of(P.ph, P.cost_kind, tab, word);
-          if (P.ph.mode != 0) ph = cmulf(ph, P.scl_phase);
-          v[r] = cmulf(v[r], ph);
-          w[r] = cmulf(w[r], ph);
-        }
+        const int m = phase_m(P.ph);
+        if (m == 2)
+          unphase_round<PL, NR - 1, 2>(v, w, cb, P, tab, ag);
+        else if (m == 3)
+          unphase_round<PL, NR - 1, 3>(v, w, cb, P, tab, ag);
+        else
+          unphase_round<PL, NR - 1, 1>(v, w, cb, P, tab, ag);
       }
       constexpr bool final0 = H2;
       if constexpr (H2) {

@@ -60,10 +60,12 @@ PROBLEM_LABS, PROBLEM_MAXCUT = 0, 1
 
 
 class CostStats(C.Structure):
-    _fields_ = [("f_min", C.c_double), ("f_max", C.c_double), ("n_min", C.c_uint64)]
+    _fields_ = [("f_min", C.c_double), ("f_max", C.c_double), ("n_min", C.c_uint64),
+                ("step_log2", C.c_uint32), ("reserved", C.c_uint32)]
 
     def __repr__(self):
-        return f"CostStats(f_min={self.f_min}, f_max={self.f_max}, n_min={self.n_min})"
+        return (f"CostStats(f_min={self.f_min}, f_max={self.f_max}, n_min={self.n_min}, "
+                f"step_log2={self.step_log2})")
 
 
 _lib = None

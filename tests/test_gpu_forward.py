@@ -100,6 +100,50 @@ def test_large_range_integer_costs_use_computed_phase(Q, n):
         assert rel_state_err(got, ref) < TOL[st]["state"]
 
 
+@pytest.mark.parametrize("n", [13, 17])
+@pytest.mark.parametrize("terms,shift,digits", [
+    # weights multiples of 4: every f - f_min a multiple of 8, range 1120
+    ([(400, (0, 1)), (148, (2,)), (12, (3, 4))], 3, 2),
+    # range 11022 >> 1 = 5511: more than two 6-bit digit tables hold
+    ([(4001, (0, 1)), (1503, (2,)), (7, (3, 4, 5))], 1, 3),
+])
+def test_integer_phase_tables(Q, n, terms, shift, digits):
+    # the table phase of integer costs indexes (f - f_min) >> step_log2 in
+    # two or three digits; both layouts against the oracle
+    f = oracle.costs_terms_int(n, terms)
+    d = (f - f.min()).astype(np.int64)
+    assert np.bitwise_or.reduce(d) & ((1 << shift) - 1) == 0
+    fd = Q.precompute_costs(n, terms, Q.COST_I32)
+    stats = Q.cost_stats_compute(fd)
+    assert stats.step_log2 == shift
+    rr = int(d.max()) >> shift
+    assert (rr >> 6) + 1 + 64 <= 112 if digits == 2 else (rr >> 6) + 1 + 64 > 112
+    g = [0.021, 0.0047, 0.3]
+    b = [0.4, 1.1, 2.9]
+    got, ref, o, E, O = run_case(Q, n, f.astype(float), fd, g, b, "c64")
+    assert rel_state_err(got, ref) < TOL["c64"]["state"]
+    assert abs(o[0] - E) <= TOL["c64"]["energy"] * max(1.0, abs(E))
+
+
+def test_cost_stats_step(Q):
+    # step_log2 = lowest set bit of OR_x (f[x] - f_min), int32 costs only
+    T = torch()
+    n = 14
+    fd = Q.labs_costs(n)
+    f = oracle.labs_costs(n).astype(np.int64)
+    bits = int(np.bitwise_or.reduce(f - f.min()))
+    step = Q.cost_stats_compute(fd).step_log2
+    assert step == (bits & -bits).bit_length() - 1 and step >= 2  # LABS: f = f_min mod 4
+    edges, w = I.maxcut_3reg(n, graph_seed=5)
+    f = oracle.maxcut_costs(n, edges, w).astype(np.int64)
+    fd = Q.maxcut_costs(n, edges, w, Q.COST_I32)
+    bits = int(np.bitwise_or.reduce(f - f.min()))
+    want = (bits & -bits).bit_length() - 1 if bits else 0
+    assert Q.cost_stats_compute(fd).step_log2 == want
+    fd32 = T.as_tensor(f.astype(np.float32) * 4).to("cuda")
+    assert Q.cost_stats_compute(fd32).step_log2 == 0  # float costs: no step
+
+
 @pytest.mark.parametrize("n", [10, 15])
 def test_trivial_angles(Q, n):
     # gamma = beta = 0: E = mean(f), O = #argmin / 2^n

@@ -386,3 +386,13 @@ def test_uncompute_recovers_plus(orc):
         psi = orc.apply_mixer(n, psi, -b[l])
         psi = orc.apply_phase(n, psi, f, -g[l])
     np.testing.assert_allclose(psi, orc.init_plus(n), atol=1e-13)
+
+
+@pytest.mark.parametrize("n", range(2, 17))
+def test_labs_costs_congruent_mod_4(orc, n):
+    # C_k = sum_i s_i s_{i+k} has n - k terms of +-1, so C_k = n - k (mod 2);
+    # an odd square is 1 mod 8 and an even one 0 mod 4, hence f = sum C_k^2 is
+    # the number of k in 1..n-1 with n - k odd, mod 4, for every bitstring
+    f = orc.labs_costs(n).astype(np.int64)
+    odd = sum(1 for k in range(1, n) if (n - k) % 2)
+    assert np.all(f % 4 == odd % 4)
