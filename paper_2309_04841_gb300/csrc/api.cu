@@ -444,8 +444,12 @@ std::vector<PassOp> adjoint_schedule(int k, int p) {
     for (int l = p - 1; l >= 0; --l) ops.push_back(PassOp{0, l, l, -1, l == p - 1, false});
     return ops;
   }
+  // The pivot alternates between the two ends of the order; with three or
+  // more groups the LOW group (0, three rounds per sweep) goes second, so it
+  // never carries two sweeps and the phase in one pass.
   std::vector<int> order(k);
   for (int i = 0; i < k; ++i) order[i] = i;
+  if (k >= 3) std::swap(order[0], order[1]);
   for (int l = p - 1; l >= 0; --l) {
     if (l == p - 1) ops.push_back(PassOp{order[0], l, -1, -1, true, false});
     for (int i = 1; i + 1 < k; ++i) ops.push_back(PassOp{order[i], l, -1, -1, false, false});

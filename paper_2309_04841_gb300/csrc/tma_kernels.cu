@@ -169,18 +169,21 @@ template <int EB>
 __device__ __forceinline__ void unrot_tw(float2 (&v)[1 << EB], float2 (&w)[1 << EB], uint32_t m,
                                          float tau, int form, float wr, float &acc) {
   if (m == 0u) return;
-  float2 pp = f2(0.f, 0.f), pm = f2(0.f, 0.f);
+  // two accumulator pairs (by register parity) halve the dependency chains
+  float2 pp[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, pm[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
 #pragma unroll
   for (int i = 0; i < EB; ++i)
     if ((m >> i) & 1u) {
 #pragma unroll
       for (int r = 0; r < (1 << EB); ++r)
         if (!((r >> i) & 1)) {
-          pp = __ffma2_rn(w[r], v[r | (1 << i)], pp);
-          pm = __ffma2_rn(w[r | (1 << i)], v[r], pm);
+          const int k = (r >> (i == 0 ? 1 : 0)) & 1;
+          pp[k] = __ffma2_rn(w[r], v[r | (1 << i)], pp[k]);
+          pm[k] = __ffma2_rn(w[r | (1 << i)], v[r], pm[k]);
         }
     }
-  acc = fmaf((pp.x + pp.y) - (pm.x + pm.y), wr, acc);
+  const float2 sp = __fadd2_rn(pp[0], pp[1]), sm = __fadd2_rn(pm[0], pm[1]);
+  acc = fmaf((sp.x + sp.y) - (sm.x + sm.y), wr, acc);
   rot_tw<EB>(v, m, tau, form);
   rot_tw<EB>(w, m, tau, form);
 }
