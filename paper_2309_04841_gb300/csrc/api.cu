@@ -630,6 +630,7 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
     memset(&P, 0, sizeof(P));
     const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
     CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, 128), "tensor map (state)");
+    P.psi = reinterpret_cast<float2 *>(state);
     CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, 4, 0), "tensor map (cost)");
     P.ntiles = 1ull << (n - TB);
     P.h = h;
@@ -704,6 +705,8 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     const int sw = 128;
     CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, sw), "tensor map (psi)");
     CK(make_tile_map(&P.map_lam, lam, n, TB, h, c, 8, sw), "tensor map (lambda)");
+    P.psi = reinterpret_cast<float2 *>(state);
+    P.lam = reinterpret_cast<float2 *>(lam);
     CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, 4, 0), "tensor map (cost)");
     P.ntiles = 1ull << (n - TB);
     P.h = h;

@@ -101,8 +101,9 @@ struct PhaseDigits {
 };
 
 struct alignas(64) TmaFwdParams {
-  CUtensorMap map_psi;   // state, 8-byte elements, 128-byte swizzle
+  CUtensorMap map_psi;   // state, 8-byte elements, 128-byte swizzle (loads)
   CUtensorMap map_cost;  // cost vector, 4-byte elements
+  float2 *psi;           // the state (finished tiles are stored from registers)
   uint64_t ntiles;
   int h, c, cost_kind;  // tile = 2^c contiguous amplitudes x rows at qubits h..
   Sweep s1, s2;
@@ -123,7 +124,8 @@ struct alignas(64) TmaFwdParams {
 };
 
 struct alignas(64) TmaBwdParams {
-  CUtensorMap map_psi, map_lam, map_cost;
+  CUtensorMap map_psi, map_lam, map_cost;  // loads
+  float2 *psi, *lam;                       // stores, from registers
   uint64_t ntiles;
   int h, c, cost_kind;
   Sweep s1, s2;

@@ -47,10 +47,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -85,26 +81,10 @@ __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, TC c
       : "memory");
 }
 
-__device__ __forceinline__ void tma_store(const CUtensorMap *map, const void *src, TC c) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group"
-      " [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
-      "r"(smem_u32(src)), "r"(0), "r"(c.x1), "r"(c.x2), "r"(0), "r"(c.x4)
-      : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() {
-  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-// Barrier among the 256 compute threads only (the producer warp never joins).
+// Barrier among the CTA's 256 threads (named barrier 1).
 __device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // TMA swizzle seen at 8-byte granularity.  SWIZZLE_128B: the 16-byte chunk
@@ -257,6 +237,17 @@ __device__ __forceinline__ void xp(float2 (&v)[PL::NREG], float2 *buf) {
   sts_round<PL, RF, SW>(v, buf);
   cbar();
   lds_round<PL, RT, SW>(v, buf);
+}
+
+// The same for psi and lambda together (one barrier).
+template <class PL, int RF, int RT, int SW>
+__device__ __forceinline__ void xp_pair(float2 (&v)[PL::NREG], float2 (&w)[PL::NREG], float2 *bv,
+                                        float2 *bw) {
+  sts_round<PL, RF, SW>(v, bv);
+  sts_round<PL, RF, SW>(w, bw);
+  cbar();
+  lds_round<PL, RT, SW>(v, bv);
+  lds_round<PL, RT, SW>(w, bw);
 }
 
 // exp(-i g f) from the raw 32-bit cost word (int32 or float32).
@@ -419,23 +410,50 @@ __device__ __forceinline__ void final_reduce(const double *partials, uint64_t np
   }
 }
 
-// Shared-memory layout (offsets from a 1024-byte aligned base): two stage
-// buffers of the state (and lambda), two of the cost vector, the phase
-// tables, the mbarriers and the reduction scratch.
+// Shared-memory layout (offsets from a 1024-byte aligned base): the state
+// tile (and the lambda tile), the cost tile, the phase tables, the mbarrier
+// and the reduction scratch.
 struct Lay {
   uint32_t tile_bytes, lam_off, cost_off, cost_bytes, tab_off, bar_off, red_off;
 };
 
-__device__ __forceinline__ Lay layout(uint32_t tile_elems, bool two, bool cost, uint32_t ns) {
+__device__ __forceinline__ Lay layout(uint32_t tile_elems, bool two, bool cost) {
   Lay L;
   L.tile_bytes = tile_elems * 8u;
-  L.lam_off = ns * L.tile_bytes;
-  L.cost_off = L.lam_off + (two ? ns * L.tile_bytes : 0u);
+  L.lam_off = L.tile_bytes;
+  L.cost_off = L.lam_off + (two ? L.tile_bytes : 0u);
   L.cost_bytes = cost ? tile_elems * 4u : 0u;
-  L.tab_off = L.cost_off + ns * L.cost_bytes;
+  L.tab_off = L.cost_off + L.cost_bytes;
   L.bar_off = L.tab_off + (uint32_t)kPhaseTabEntries * 8u;
   L.red_off = L.bar_off + 32u;
   return L;
+}
+
+// Registers (round-R layout) -> the state vector in HBM, straight from the
+// registers: tile offset t of tile T is amplitude
+//   x = (t & (2^c - 1)) | (mid << c) | ((t >> c) << h) | (top << (h + TB - c)),
+// mid / top the low h - c / remaining bits of T.  In every round the 32 lanes
+// of a warp cover whole 128-byte segments, so the stores are coalesced.
+template <class PL, int R>
+__device__ __forceinline__ void stg_round(const float2 (&v)[PL::NREG], float2 *g, uint64_t T,
+                                          int h, int c) {
+  constexpr uint32_t RM = PL::reg(R);
+  const int midbits = h - c;
+  const uint32_t cm = (1u << c) - 1u;
+  auto f = [&](uint32_t t) -> uint64_t { return (uint64_t)(t & cm) | ((uint64_t)(t >> c) << h); };
+  const uint64_t mid = T & ((1ull << midbits) - 1ull), top = T >> midbits;
+  float2 *b = g + ((mid << c) | (top << (h + PL::TB - c))) + f(thr_tile<PL, R>());
+  uint64_t u[PL::EB];  // offset of each register bit
+#pragma unroll
+  for (int k = 0; k < PL::EB; ++k) u[k] = f(pdep(1u << k, RM));
+#pragma unroll
+  for (int r = 0; r < PL::NREG; ++r) {
+    uint64_t off = 0;
+#pragma unroll
+    for (int k = 0; k < PL::EB; ++k)
+      if ((r >> k) & 1) off += u[k];
+    b[off] = v[r];
+  }
 }
 
 __device__ __forceinline__ unsigned char *aligned_base(unsigned char *raw) {
@@ -445,52 +463,57 @@ __device__ __forceinline__ unsigned char *aligned_base(unsigned char *raw) {
 
 }  // namespace
 
-size_t tma_smem_bytes(int tb, bool two, bool cost, int ns) {
+size_t tma_smem_bytes(int tb, bool two, bool cost) {
   const size_t te = (size_t)1 << tb;
-  return 1024 + ns * te * 8 * (two ? 2 : 1) + (cost ? ns * te * 4 : 0) + kPhaseTabEntries * 8 + 32 +
-         8 * 3 * 8;
+  return 1024 + te * 8 * (two ? 2 : 1) + (cost ? te * 4 : 0) + kPhaseTabEntries * 8 + 32 + 8 * 3 * 8;
 }
 
 // ------------------------------------------------------------- forward
 //
-// NS = 2: 8 compute warps + 1 producer warp, two stages per CTA, one CTA per
-//         SM; the producer keeps the next tile's load in flight.
-// NS = 1: 8 compute warps, one stage per CTA, two CTAs per SM; thread 0
-//         issues the store and the next load between tiles, and the other
-//         CTA on the SM computes meanwhile.
+// Persistent CTAs, two per SM (256 threads, at most 128 registers), one tile
+// buffer each.  Thread 0 loads a tile with TMA; the 8 warps run the rounds
+// (shared-memory transposes between them); once the last round's data is in
+// registers the buffer goes to the next tile's load, and the finished tile
+// is written from the registers straight to HBM while that load is in flight.
+// The other CTA on the SM computes meanwhile.
 
-template <int NS> struct TmaCfg {
-  static constexpr int NT = NS == 1 ? 256 : 288;
-  static constexpr int MINB = NS == 1 ? 2 : 1;
-};
+constexpr int kThreads = 256;
+
+// After a timed-out wait the loop was left early, possibly with the load of
+// tile i (issued by the previous tile's release) still in flight: wait for
+// it, again bounded, before the CTA exits.
+__device__ __forceinline__ void drain(int aborted, uint64_t *full, int i, uint64_t ntiles) {
+  if (aborted && threadIdx.x == 0 && blockIdx.x + (uint64_t)i * gridDim.x < ntiles)
+    (void)mbar_wait(full, i & 1);
+}
 
 // Pass kinds, fixed at compile time so each instantiation carries only its
 // own path: forward  K = kH1 | kPH | kH2 | kRED,  adjoint  K = kPH | kH2 | kINIT.
 constexpr int kH1 = 1, kPH = 2, kH2 = 4, kRED = 8, kINIT = 8;
 
-template <class PL, int NS, int SW, int K>
-__global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
-    k_fwd_tma(const __grid_constant__ TmaFwdParams P) {
-  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, NT = TmaCfg<NS>::NT;
+template <class PL, int K>
+__global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__ TmaFwdParams P) {
+  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, SW = 128;
   constexpr bool H1 = (K & kH1) != 0, PH = (K & kPH) != 0, H2 = (K & kH2) != 0, RED = (K & kRED) != 0;
-  extern __shared__ unsigned char smem_raw[];
+  static_assert(!(H1 && PH && !H2), "a first sweep with the phase always has a second sweep");
   constexpr bool need_cost = PH || RED;
+  constexpr int RS = (H1 && H2) ? 0 : NR - 1;  // the round the tile is stored from
+  extern __shared__ unsigned char smem_raw[];
   unsigned char *base = aligned_base(smem_raw);
-  const Lay L = layout(1u << PL::TB, false, need_cost, NS);
+  const Lay L = layout(1u << PL::TB, false, need_cost);
+  float2 *buf = reinterpret_cast<float2 *>(base);
+  const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off);
   float2 *tab = reinterpret_cast<float2 *>(base + L.tab_off);
-  uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off), *empty = full + 2;
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off);
   double *red = reinterpret_cast<double *>(base + L.red_off);
   const int tid = threadIdx.x;
   const int midbits = P.h - P.c;
   __shared__ int s_abort;
 
-  if (PH && P.ph.mode == 0) fill_phase_tab<NT>(tab, P.ph);
+  if (PH && P.ph.mode == 0) fill_phase_tab<kThreads>(tab, P.ph);
   if (tid == 0) {
     s_abort = 0;
-    for (int s = 0; s < NS; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 256);
-    }
+    mbar_init(full, 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -505,153 +528,108 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     c.x4 = (int)(T >> midbits);
     return c;
   };
-  auto issue = [&](uint64_t T, int s) {
+  auto issue = [&](uint64_t T) {
     const TC c = coords(T);
-    mbar_expect_tx(&full[s], (P.init_plus ? 0u : L.tile_bytes) + (need_cost ? L.cost_bytes : 0u));
-    if (!P.init_plus) tma_load(base + s * L.tile_bytes, &P.map_psi, c, &full[s]);
-    if (need_cost) tma_load(base + L.cost_off + s * L.cost_bytes, &P.map_cost, c, &full[s]);
+    mbar_expect_tx(full, (P.init_plus ? 0u : L.tile_bytes) + (need_cost ? L.cost_bytes : 0u));
+    if (!P.init_plus) tma_load(buf, &P.map_psi, c, full);
+    if (need_cost) tma_load(base + L.cost_off, &P.map_cost, c, full);
+  };
+  // after the tile's last shared-memory read: the buffers go to the next load
+  auto release = [&](uint64_t T) {
+    cbar();
+    if (tid == 0 && T + gridDim.x < P.ntiles) issue(T + gridDim.x);
   };
 
-  if (tid == (NS == 1 ? 0 : 256))
-    for (int i = 0; i < NS; ++i) {
-      const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
-      if (T < P.ntiles) issue(T, i);
-    }
+  if (tid == 0 && blockIdx.x < P.ntiles) issue(blockIdx.x);
 
-  if (NS == 2 && tid >= 256) {
-    // ---------------- producer warp: stores of finished tiles, next loads
-    if (tid == 256) {
-      for (int i = 0;; ++i) {
-        const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
-        if (T >= P.ntiles) break;
-        const int s = i % NS;
-        if (!mbar_wait(&empty[s], (i / NS) & 1)) {
-          atomicExch(P.err, 1u);
-          break;
-        }
-        const TC c = coords(T);
-        tma_store(&P.map_psi, base + s * L.tile_bytes, c);
-        bulk_commit();
-        const uint64_t T2 = T + (uint64_t)NS * gridDim.x;
-        if (T2 < P.ntiles) {
-          bulk_wait_read0();
-          issue(T2, s);
-        }
-      }
-      bulk_wait0();
+  FF acc_e, acc_o;  // this thread's energy / overlap terms
+  int i = 0;
+  for (;; ++i) {
+    const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
+    if (T >= P.ntiles) break;
+    // A timed-out wait flags the abort and still runs this tile (on stale
+    // data) through the same barriers as every other thread; all threads
+    // see the flag after those barriers and leave together.
+    if (s_abort) break;
+    if (!mbar_wait(full, i & 1)) {
+      s_abort = 1;
+      atomicExch(P.err, 1u);
     }
-  } else {
-    // ---------------- compute warps
-    FF acc_e, acc_o;  // this thread's energy / overlap terms
-    for (int i = 0;; ++i) {
-      const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
-      if (T >= P.ntiles) break;
-      const int s = i % NS;
-      // A timed-out wait flags the abort and still runs this tile (on stale
-      // data) through the same barriers as every other thread; all threads
-      // see the flag after those barriers and leave together.
-      if (s_abort) break;
-      if (!mbar_wait(&full[s], (i / NS) & 1)) {
-        s_abort = 1;
-        atomicExch(P.err, 1u);
-      }
-      float2 *buf = reinterpret_cast<float2 *>(base + s * L.tile_bytes);
-      const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off + s * L.cost_bytes);
-      float2 v[NREG];
-      if (P.init_plus) {
-        // |+>^n in the twisted basis: amp (-i)^popc(x)
-        const int b0 = twist_base<PL, 0>(T);
+    float2 v[NREG];
+    if (P.init_plus) {
+      // |+>^n in the twisted basis: amp (-i)^popc(x)
+      const float2 z0 = ipow(f2(P.amp, 0.f), -twist_base<PL, 0>(T));
 #pragma unroll
-        for (int r = 0; r < NREG; ++r) v[r] = ipow(f2(P.amp, 0.f), -(b0 + popc_c(r)));
-      } else {
-        lds_round<PL, 0, SW>(v, buf);
-        if (P.twist_in) {
-          const float2 z = ipow(f2(1.f, 0.f), -twist_base<PL, 0>(T));
+      for (int r = 0; r < NREG; ++r) v[r] = ipow(z0, -popc_c(r));
+    } else {
+      lds_round<PL, 0, SW>(v, buf);
+      if (P.twist_in) {
+        const float2 z = ipow(f2(1.f, 0.f), -twist_base<PL, 0>(T));
 #pragma unroll
-          for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), -popc_c(r));
-        }
+        for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), -popc_c(r));
       }
-      constexpr bool final0 = H1 && H2;  // s2 walks back down to round 0
-      if constexpr (H1) {
-        rot_tw<EB>(v, P.s1.m[0], P.tau1, P.form1);
-        xp<PL, 0, 1, SW>(v, buf);
-        rot_tw<EB>(v, P.s1.m[1], P.tau1, P.form1);
+    }
+    if constexpr (H1) {
+      rot_tw<EB>(v, P.s1.m[0], P.tau1, P.form1);
+      xp<PL, 0, 1, SW>(v, buf);
+      if constexpr (NR == 2 && !H2 && !RED) release(T);
+      rot_tw<EB>(v, P.s1.m[1], P.tau1, P.form1);
+      if constexpr (NR == 3) {
+        xp<PL, 1, 2, SW>(v, buf);
+        if constexpr (!H2 && !RED) release(T);
+        rot_tw<EB>(v, P.s1.m[2], P.tau1, P.form1);
+      }
+      if constexpr (PH) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tab, P.scl_phase);
+      if constexpr (H2) {
+        rot_tw<EB>(v, P.s2.m[NR - 1], P.tau2, P.form2);
         if constexpr (NR == 3) {
-          xp<PL, 1, 2, SW>(v, buf);
-          rot_tw<EB>(v, P.s1.m[2], P.tau1, P.form1);
+          xp<PL, 2, 1, SW>(v, buf);
+          rot_tw<EB>(v, P.s2.m[1], P.tau2, P.form2);
         }
-        if constexpr (PH) phase_round<PL, NR - 1>(v, cb, P.ph, P.cost_kind, tab, P.scl_phase);
-        if constexpr (H2) {
-          rot_tw<EB>(v, P.s2.m[NR - 1], P.tau2, P.form2);
-          if constexpr (NR == 3) {
-            xp<PL, 2, 1, SW>(v, buf);
-            rot_tw<EB>(v, P.s2.m[1], P.tau2, P.form2);
-          }
-          xp<PL, 1, 0, SW>(v, buf);
-          rot_tw<EB>(v, P.s2.m[0], P.tau2, P.form2);
-        }
-      } else {
-        if constexpr (PH) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tab, P.scl_phase);
+        xp<PL, 1, 0, SW>(v, buf);
+        if constexpr (!RED) release(T);
         rot_tw<EB>(v, P.s2.m[0], P.tau2, P.form2);
-        xp<PL, 0, 1, SW>(v, buf);
-        rot_tw<EB>(v, P.s2.m[1], P.tau2, P.form2);
-        if constexpr (NR == 3) {
-          xp<PL, 1, 2, SW>(v, buf);
-          rot_tw<EB>(v, P.s2.m[2], P.tau2, P.form2);
-        }
       }
-      constexpr int RS = (H1 && H2) ? 0 : NR - 1;  // the round the tile is stored from
-      if (P.end_scale) {
-        if (P.untwist) {
-          // back to the standard basis: psi(x) = i^popc(x) s(x)
-          const float2 z = cmulf(P.scl_end, ipow(f2(1.f, 0.f), twist_base<PL, RS>(T)));
-#pragma unroll
-          for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), popc_c(r));
-        } else {
-#pragma unroll
-          for (int r = 0; r < NREG; ++r) v[r] = cmulf(v[r], P.scl_end);
-        }
-      }
-      float e = 0.f, o = 0.f;
-      if constexpr (final0) {
-        if constexpr (RED) eo_round<PL, 0>(v, cb, P.cost_kind, P.fmin_word, e, o);
-        sts_round<PL, 0, SW>(v, buf);
-      } else {
-        if constexpr (RED) eo_round<PL, NR - 1>(v, cb, P.cost_kind, P.fmin_word, e, o);
-        sts_round<PL, NR - 1, SW>(v, buf);
-      }
-      fence_async_smem();
-      if constexpr (NS == 2) {
-        mbar_arrive(&empty[s]);
-      } else {
-        cbar();
-        if (tid == 0) {
-          const TC c = coords(T);
-          tma_store(&P.map_psi, buf, c);
-          bulk_commit();
-          const uint64_t T2 = T + gridDim.x;
-          if (T2 < P.ntiles) {
-            bulk_wait_read0();
-            issue(T2, 0);
-          }
-        }
-      }
-      if constexpr (RED) {
-        acc_e.add(e);
-        acc_o.add(o);
+    } else {
+      if constexpr (PH) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tab, P.scl_phase);
+      rot_tw<EB>(v, P.s2.m[0], P.tau2, P.form2);
+      xp<PL, 0, 1, SW>(v, buf);
+      if constexpr (NR == 2 && !RED) release(T);
+      rot_tw<EB>(v, P.s2.m[1], P.tau2, P.form2);
+      if constexpr (NR == 3) {
+        xp<PL, 1, 2, SW>(v, buf);
+        if constexpr (!RED) release(T);
+        rot_tw<EB>(v, P.s2.m[2], P.tau2, P.form2);
       }
     }
-    if (NS == 1 && tid == 0) bulk_wait0();
+    if (P.end_scale) {
+      if (P.untwist) {
+        // back to the standard basis: psi(x) = i^popc(x) s(x)
+        const float2 z = cmulf(P.scl_end, ipow(f2(1.f, 0.f), twist_base<PL, RS>(T)));
+#pragma unroll
+        for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), popc_c(r));
+      } else {
+#pragma unroll
+        for (int r = 0; r < NREG; ++r) v[r] = cmulf(v[r], P.scl_end);
+      }
+    }
     if constexpr (RED) {
-      double a[2] = {acc_e.value(), acc_o.value()};
-      csum<2>(a, red);
-      if (tid == 0) {
-        P.partials[blockIdx.x * 2] = a[0];
-        P.partials[blockIdx.x * 2 + 1] = a[1];
-      }
+      float e = 0.f, o = 0.f;
+      eo_round<PL, RS>(v, cb, P.cost_kind, P.fmin_word, e, o);
+      acc_e.add(e);
+      acc_o.add(o);
+      release(T);
     }
+    stg_round<PL, RS>(v, P.psi, T, P.h, P.c);
   }
+  drain(s_abort, full, i, P.ntiles);
   if constexpr (RED) {
+    double a[2] = {acc_e.value(), acc_o.value()};
+    csum<2>(a, red);
+    if (tid == 0) {
+      P.partials[blockIdx.x * 2] = a[0];
+      P.partials[blockIdx.x * 2 + 1] = a[1];
+    }
     double *out = P.out;
     final_reduce<2>(P.partials, gridDim.x, P.counter, red, [out](double(&a)[2]) {
       out[0] = a[0];
@@ -681,29 +659,29 @@ __device__ __forceinline__ void unphase_round(float2 (&v)[PL::NREG], float2 (&w)
   }
 }
 
-template <class PL, int NS, int SW, int K>
-__global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
-    k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
-  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, NT = TmaCfg<NS>::NT;
+template <class PL, int K>
+__global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
+  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, SW = 128;
   constexpr bool PH = (K & kPH) != 0, H2 = (K & kH2) != 0, INIT = (K & kINIT) != 0;
-  extern __shared__ unsigned char smem_raw[];
   constexpr bool need_cost = PH || INIT;
+  constexpr int RS = H2 ? 0 : NR - 1;  // the round the tiles are stored from
+  extern __shared__ unsigned char smem_raw[];
   unsigned char *base = aligned_base(smem_raw);
-  const Lay L = layout(1u << PL::TB, true, need_cost, NS);
+  const Lay L = layout(1u << PL::TB, true, need_cost);
+  float2 *bv = reinterpret_cast<float2 *>(base);
+  float2 *bw = reinterpret_cast<float2 *>(base + L.lam_off);
+  const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off);
   float2 *tab = reinterpret_cast<float2 *>(base + L.tab_off);
-  uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off), *empty = full + 2;
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off);
   double *red = reinterpret_cast<double *>(base + L.red_off);
   const int tid = threadIdx.x;
   const int midbits = P.h - P.c;
   __shared__ int s_abort;
 
-  if (PH && P.ph.mode == 0) fill_phase_tab<NT>(tab, P.ph);
+  if (PH && P.ph.mode == 0) fill_phase_tab<kThreads>(tab, P.ph);
   if (tid == 0) {
     s_abort = 0;
-    for (int s = 0; s < NS; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 256);
-    }
+    mbar_init(full, 1);
     fence_mbar_init();
   }
   __syncthreads();
@@ -718,159 +696,96 @@ __global__ void __launch_bounds__(TmaCfg<NS>::NT, TmaCfg<NS>::MINB)
     c.x4 = (int)(T >> midbits);
     return c;
   };
-  auto issue = [&](uint64_t T, int s) {
+  auto issue = [&](uint64_t T) {
     const TC c = coords(T);
-    mbar_expect_tx(&full[s], L.tile_bytes + (INIT ? 0u : L.tile_bytes) +
-                                 (need_cost ? L.cost_bytes : 0u));
-    tma_load(base + s * L.tile_bytes, &P.map_psi, c, &full[s]);
-    if (!INIT) tma_load(base + L.lam_off + s * L.tile_bytes, &P.map_lam, c, &full[s]);
-    if (need_cost) tma_load(base + L.cost_off + s * L.cost_bytes, &P.map_cost, c, &full[s]);
+    mbar_expect_tx(full, L.tile_bytes + (INIT ? 0u : L.tile_bytes) + (need_cost ? L.cost_bytes : 0u));
+    tma_load(bv, &P.map_psi, c, full);
+    if (!INIT) tma_load(bw, &P.map_lam, c, full);
+    if (need_cost) tma_load(base + L.cost_off, &P.map_cost, c, full);
   };
-  auto store = [&](uint64_t T, int s) {
-    const TC c = coords(T);
-    tma_store(&P.map_psi, base + s * L.tile_bytes, c);
-    tma_store(&P.map_lam, base + L.lam_off + s * L.tile_bytes, c);
-    bulk_commit();
+  // after the tile's last shared-memory read: the buffers go to the next load
+  auto release = [&](uint64_t T) {
+    cbar();
+    if (tid == 0 && T + gridDim.x < P.ntiles) issue(T + gridDim.x);
   };
+  if (tid == 0 && blockIdx.x < P.ntiles) issue(blockIdx.x);
 
-  if (tid == (NS == 1 ? 0 : 256))
-    for (int i = 0; i < NS; ++i) {
-      const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
-      if (T < P.ntiles) issue(T, i);
+  FF acc1, accg, acc2;  // this thread's gradient terms
+  int i = 0;
+  for (;; ++i) {
+    const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
+    if (T >= P.ntiles) break;
+    // A timed-out wait flags the abort and still runs this tile (on stale
+    // data) through the same barriers as every other thread; all threads
+    // see the flag after those barriers and leave together.
+    if (s_abort) break;
+    if (!mbar_wait(full, i & 1)) {
+      s_abort = 1;
+      atomicExch(P.err, 1u);
     }
-
-  if (NS == 2 && tid >= 256) {
-    if (tid == 256) {
-      for (int i = 0;; ++i) {
-        const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
-        if (T >= P.ntiles) break;
-        const int s = i % NS;
-        if (!mbar_wait(&empty[s], (i / NS) & 1)) {
-          atomicExch(P.err, 1u);
-          break;
-        }
-        store(T, s);
-        const uint64_t T2 = T + (uint64_t)NS * gridDim.x;
-        if (T2 < P.ntiles) {
-          bulk_wait_read0();
-          issue(T2, s);
-        }
-      }
-      bulk_wait0();
-    }
-  } else {
-    FF acc1, accg, acc2;  // this thread's gradient terms
-    for (int i = 0;; ++i) {
-      const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
-      if (T >= P.ntiles) break;
-      const int s = i % NS;
-      // A timed-out wait flags the abort and still runs this tile (on stale
-      // data) through the same barriers as every other thread; all threads
-      // see the flag after those barriers and leave together.
-      if (s_abort) break;
-      if (!mbar_wait(&full[s], (i / NS) & 1)) {
-        s_abort = 1;
-        atomicExch(P.err, 1u);
-      }
-      float2 *bv = reinterpret_cast<float2 *>(base + s * L.tile_bytes);
-      float2 *bw = reinterpret_cast<float2 *>(base + L.lam_off + s * L.tile_bytes);
-      const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off + s * L.cost_bytes);
-      float2 v[NREG], w[NREG];
-      lds_round<PL, 0, SW>(v, bv);
-      if constexpr (INIT) {
-        // lambda = f psi: the derivative of E = <psi|f|psi> with respect to psi^*
-        const uint32_t tt = thr_tile<PL, 0>();
+    float2 v[NREG], w[NREG];
+    lds_round<PL, 0, SW>(v, bv);
+    if constexpr (INIT) {
+      // lambda = f psi: the derivative of E = <psi|f|psi> with respect to psi^*
+      const uint32_t tt = thr_tile<PL, 0>();
 #pragma unroll
-        for (int r = 0; r < NREG; ++r) {
-          const float f = cost_val(P.cost_kind, cb[tt | pdep(r, PL::reg(0))]);
-          w[r] = f2(f * v[r].x, f * v[r].y);
-        }
-      } else {
-        lds_round<PL, 0, SW>(w, bw);
+      for (int r = 0; r < NREG; ++r) {
+        const float f = cost_val(P.cost_kind, cb[tt | pdep(r, PL::reg(0))]);
+        w[r] = f2(f * v[r].x, f * v[r].y);
       }
-      float a1 = 0.f, ag = 0.f, a2 = 0.f;
-      unrot_tw<EB>(v, w, P.s1.m[0], P.tau1, P.form1, P.w1[0], a1);
-      sts_round<PL, 0, SW>(v, bv);
-      sts_round<PL, 0, SW>(w, bw);
-      cbar();
-      lds_round<PL, 1, SW>(v, bv);
-      lds_round<PL, 1, SW>(w, bw);
-      unrot_tw<EB>(v, w, P.s1.m[1], P.tau1, P.form1, P.w1[1], a1);
+    } else {
+      lds_round<PL, 0, SW>(w, bw);
+    }
+    float a1 = 0.f, ag = 0.f, a2 = 0.f;
+    unrot_tw<EB>(v, w, P.s1.m[0], P.tau1, P.form1, P.w1[0], a1);
+    xp_pair<PL, 0, 1, SW>(v, w, bv, bw);
+    if constexpr (NR == 2 && !PH && !H2) release(T);
+    unrot_tw<EB>(v, w, P.s1.m[1], P.tau1, P.form1, P.w1[1], a1);
+    if constexpr (NR == 3) {
+      xp_pair<PL, 1, 2, SW>(v, w, bv, bw);
+      if constexpr (!PH && !H2) release(T);
+      unrot_tw<EB>(v, w, P.s1.m[2], P.tau1, P.form1, P.w1[2], a1);
+    }
+    if constexpr (PH) {
+      // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
+      const int m = phase_m(P.ph);
+      if (m == 2)
+        unphase_round<PL, NR - 1, 2>(v, w, cb, P, tab, ag);
+      else if (m == 3)
+        unphase_round<PL, NR - 1, 3>(v, w, cb, P, tab, ag);
+      else
+        unphase_round<PL, NR - 1, 1>(v, w, cb, P, tab, ag);
+      if constexpr (!H2) release(T);
+    }
+    if constexpr (H2) {
+      unrot_tw<EB>(v, w, P.s2.m[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
       if constexpr (NR == 3) {
-        sts_round<PL, 1, SW>(v, bv);
-        sts_round<PL, 1, SW>(w, bw);
-        cbar();
-        lds_round<PL, 2, SW>(v, bv);
-        lds_round<PL, 2, SW>(w, bw);
-        unrot_tw<EB>(v, w, P.s1.m[2], P.tau1, P.form1, P.w1[2], a1);
+        xp_pair<PL, 2, 1, SW>(v, w, bv, bw);
+        unrot_tw<EB>(v, w, P.s2.m[1], P.tau2, P.form2, P.w2[1], a2);
       }
-      if constexpr (PH) {
-        // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
-        const int m = phase_m(P.ph);
-        if (m == 2)
-          unphase_round<PL, NR - 1, 2>(v, w, cb, P, tab, ag);
-        else if (m == 3)
-          unphase_round<PL, NR - 1, 3>(v, w, cb, P, tab, ag);
-        else
-          unphase_round<PL, NR - 1, 1>(v, w, cb, P, tab, ag);
-      }
-      constexpr bool final0 = H2;
-      if constexpr (H2) {
-        unrot_tw<EB>(v, w, P.s2.m[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
-        if constexpr (NR == 3) {
-          sts_round<PL, 2, SW>(v, bv);
-          sts_round<PL, 2, SW>(w, bw);
-          cbar();
-          lds_round<PL, 1, SW>(v, bv);
-          lds_round<PL, 1, SW>(w, bw);
-          unrot_tw<EB>(v, w, P.s2.m[1], P.tau2, P.form2, P.w2[1], a2);
-        }
-        sts_round<PL, 1, SW>(v, bv);
-        sts_round<PL, 1, SW>(w, bw);
-        cbar();
-        lds_round<PL, 0, SW>(v, bv);
-        lds_round<PL, 0, SW>(w, bw);
-        unrot_tw<EB>(v, w, P.s2.m[0], P.tau2, P.form2, P.w2[0], a2);
-      }
-      if (P.untwist) {
-        // psi back to the standard basis (lambda is scratch from here on)
-        const float2 z = ipow(f2(1.f, 0.f), twist_base<PL, final0 ? 0 : NR - 1>(T));
+      xp_pair<PL, 1, 0, SW>(v, w, bv, bw);
+      release(T);
+      unrot_tw<EB>(v, w, P.s2.m[0], P.tau2, P.form2, P.w2[0], a2);
+    }
+    if (P.untwist) {
+      // psi back to the standard basis (lambda is scratch from here on)
+      const float2 z = ipow(f2(1.f, 0.f), twist_base<PL, RS>(T));
 #pragma unroll
-        for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), popc_c(r));
-      }
-      if constexpr (final0) {
-        sts_round<PL, 0, SW>(v, bv);
-        sts_round<PL, 0, SW>(w, bw);
-      } else {
-        sts_round<PL, NR - 1, SW>(v, bv);
-        sts_round<PL, NR - 1, SW>(w, bw);
-      }
-      fence_async_smem();
-      if constexpr (NS == 2) {
-        mbar_arrive(&empty[s]);
-      } else {
-        cbar();
-        if (tid == 0) {
-          store(T, 0);
-          const uint64_t T2 = T + gridDim.x;
-          if (T2 < P.ntiles) {
-            bulk_wait_read0();
-            issue(T2, 0);
-          }
-        }
-      }
-      acc1.add(a1);
-      accg.add(ag);
-      acc2.add(a2);
+      for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), popc_c(r));
     }
-    if (NS == 1 && tid == 0) bulk_wait0();
-    double a[3] = {acc1.value(), accg.value(), acc2.value()};
-    csum<3>(a, red);
-    if (tid == 0) {
-      P.partials[blockIdx.x * 3] = a[0];
-      P.partials[blockIdx.x * 3 + 1] = a[1];
-      P.partials[blockIdx.x * 3 + 2] = a[2];
-    }
+    stg_round<PL, RS>(v, P.psi, T, P.h, P.c);
+    stg_round<PL, RS>(w, P.lam, T, P.h, P.c);
+    acc1.add(a1);
+    accg.add(ag);
+    acc2.add(a2);
+  }
+  drain(s_abort, full, i, P.ntiles);
+  double a[3] = {acc1.value(), accg.value(), acc2.value()};
+  csum<3>(a, red);
+  if (tid == 0) {
+    P.partials[blockIdx.x * 3] = a[0];
+    P.partials[blockIdx.x * 3 + 1] = a[1];
+    P.partials[blockIdx.x * 3 + 2] = a[2];
   }
   double *o1 = P.out_b1, *og = P.out_g, *o2 = P.out_b2;
   final_reduce<3>(P.partials, gridDim.x, P.counter, red, [=](double(&a)[3]) {
@@ -945,88 +860,85 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <class PL, int NS, int SW, int K>
+template <class PL, int K>
 static cudaError_t launch_fwd_tma_t(const TmaFwdParams &P, cudaStream_t s, int nsm) {
-  const size_t smem = tma_smem_bytes(PL::TB, false, (K & (kPH | kRED)) != 0, NS);
-  auto kern = k_fwd_tma<PL, NS, SW, K>;
+  const size_t smem = tma_smem_bytes(PL::TB, false, (K & (kPH | kRED)) != 0);
+  auto kern = k_fwd_tma<PL, K>;
   static int nb = 0;
   if (nb == 0) {
-    const size_t mx = tma_smem_bytes(PL::TB, false, true, NS);
+    const size_t mx = tma_smem_bytes(PL::TB, false, true);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e != cudaSuccess) return e;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TmaCfg<NS>::NT, mx) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, mx) != cudaSuccess || b < 1) b = 1;
     nb = b;
   }
   uint64_t grid = (uint64_t)nsm * nb;
   if (grid > P.ntiles) grid = P.ntiles;
-  kern<<<(unsigned)grid, TmaCfg<NS>::NT, smem, s>>>(P);
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(P);
   return cudaGetLastError();
 }
 
-template <class PL, int NS, int SW, int K>
+template <class PL, int K>
 static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int nsm) {
-  const size_t smem = tma_smem_bytes(PL::TB, true, (K & (kPH | kINIT)) != 0, NS);
-  auto kern = k_bwd_tma<PL, NS, SW, K>;
+  const size_t smem = tma_smem_bytes(PL::TB, true, (K & (kPH | kINIT)) != 0);
+  auto kern = k_bwd_tma<PL, K>;
   static int nb = 0;
   if (nb == 0) {
-    const size_t mx = tma_smem_bytes(PL::TB, true, true, NS);
+    const size_t mx = tma_smem_bytes(PL::TB, true, true);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e != cudaSuccess) return e;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TmaCfg<NS>::NT, mx) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, mx) != cudaSuccess || b < 1) b = 1;
     nb = b;
   }
   uint64_t grid = (uint64_t)nsm * nb;
   if (grid > P.ntiles) grid = P.ntiles;
-  kern<<<(unsigned)grid, TmaCfg<NS>::NT, smem, s>>>(P);
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(P);
   return cudaGetLastError();
 }
 
-#ifndef QAOA_TMA_STAGES
-#define QAOA_TMA_STAGES 1
-#endif
-
-template <class PL, int NS>
+template <class PL>
 static cudaError_t dispatch_fwd(const TmaFwdParams &P, cudaStream_t s, int nsm) {
   const bool h1 = (P.s1.m[0] | P.s1.m[1] | P.s1.m[2]) != 0;
   const bool h2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2]) != 0;
   const int k = (h1 ? kH1 : 0) | (P.has_phase ? kPH : 0) | (h2 ? kH2 : 0) | (P.reduce ? kRED : 0);
   switch (k) {  // the kinds the forward schedules produce
-    case kPH | kH2: return launch_fwd_tma_t<PL, NS, 128, kPH | kH2>(P, s, nsm);
-    case kPH | kH2 | kRED: return launch_fwd_tma_t<PL, NS, 128, kPH | kH2 | kRED>(P, s, nsm);
-    case kH2: return launch_fwd_tma_t<PL, NS, 128, kH2>(P, s, nsm);
-    case kH1 | kPH | kH2: return launch_fwd_tma_t<PL, NS, 128, kH1 | kPH | kH2>(P, s, nsm);
-    case kH1: return launch_fwd_tma_t<PL, NS, 128, kH1>(P, s, nsm);
-    case kH1 | kRED: return launch_fwd_tma_t<PL, NS, 128, kH1 | kRED>(P, s, nsm);
+    case kPH | kH2: return launch_fwd_tma_t<PL, kPH | kH2>(P, s, nsm);
+    case kPH | kH2 | kRED: return launch_fwd_tma_t<PL, kPH | kH2 | kRED>(P, s, nsm);
+    case kH2: return launch_fwd_tma_t<PL, kH2>(P, s, nsm);
+    case kH1 | kPH | kH2: return launch_fwd_tma_t<PL, kH1 | kPH | kH2>(P, s, nsm);
+    case kH1: return launch_fwd_tma_t<PL, kH1>(P, s, nsm);
+    case kH1 | kRED: return launch_fwd_tma_t<PL, kH1 | kRED>(P, s, nsm);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <class PL, int NS>
+template <class PL>
 static cudaError_t dispatch_bwd(const TmaBwdParams &P, cudaStream_t s, int nsm) {
   const bool h2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2]) != 0;
   const int k = (P.has_phase ? kPH : 0) | (h2 ? kH2 : 0) | (P.init_lambda ? kINIT : 0);
   switch (k) {  // the kinds the adjoint schedules produce
-    case 0: return launch_bwd_tma_t<PL, NS, 128, 0>(P, s, nsm);
-    case kINIT: return launch_bwd_tma_t<PL, NS, 128, kINIT>(P, s, nsm);
-    case kPH | kH2: return launch_bwd_tma_t<PL, NS, 128, kPH | kH2>(P, s, nsm);
-    case kPH: return launch_bwd_tma_t<PL, NS, 128, kPH>(P, s, nsm);
-    case kPH | kINIT: return launch_bwd_tma_t<PL, NS, 128, kPH | kINIT>(P, s, nsm);
+    case 0: return launch_bwd_tma_t<PL, 0>(P, s, nsm);
+    case kINIT: return launch_bwd_tma_t<PL, kINIT>(P, s, nsm);
+    case kPH | kH2: return launch_bwd_tma_t<PL, kPH | kH2>(P, s, nsm);
+    case kPH: return launch_bwd_tma_t<PL, kPH>(P, s, nsm);
+    case kPH | kINIT: return launch_bwd_tma_t<PL, kPH | kINIT>(P, s, nsm);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm) {
-  constexpr int NS = QAOA_TMA_STAGES;
   if (P.c != 4 && P.c != 5) return cudaErrorInvalidValue;  // 16- or 32-amplitude segments
-  return high ? dispatch_fwd<PlanTmaF13High, NS>(P, s, nsm) : dispatch_fwd<PlanTmaF13Low, NS>(P, s, nsm);
+  if (!P.psi || ((uintptr_t)P.psi & 15u)) return cudaErrorInvalidValue;
+  return high ? dispatch_fwd<PlanTmaF13High>(P, s, nsm) : dispatch_fwd<PlanTmaF13Low>(P, s, nsm);
 }
 
 cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {
-  constexpr int NS = QAOA_TMA_STAGES;
   if (P.c != 4 && P.c != 5) return cudaErrorInvalidValue;  // 16- or 32-amplitude segments
-  return high ? dispatch_bwd<PlanTmaB12High, NS>(P, s, nsm) : dispatch_bwd<PlanTmaB12Low, NS>(P, s, nsm);
+  if (!P.psi || !P.lam || ((uintptr_t)P.psi & 15u) || ((uintptr_t)P.lam & 15u))
+    return cudaErrorInvalidValue;
+  return high ? dispatch_bwd<PlanTmaB12High>(P, s, nsm) : dispatch_bwd<PlanTmaB12Low>(P, s, nsm);
 }
 
 }  // namespace qaoa
