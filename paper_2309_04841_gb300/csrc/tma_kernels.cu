@@ -41,6 +41,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+// Raises the transaction count of the current phase without arriving.
+__device__ __forceinline__ void mbar_add_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
@@ -239,16 +246,31 @@ __device__ __forceinline__ void xp(float2 (&v)[PL::NREG], float2 *buf) {
   lds_round<PL, RT, SW>(v, buf);
 }
 
+// xp with `at_barrier()` run right after the barrier (all reads of the
+// previous round done), before the loads.
+template <class PL, int RF, int RT, int SW, class F>
+__device__ __forceinline__ void xp_hook(float2 (&v)[PL::NREG], float2 *buf, F at_barrier) {
+  sts_round<PL, RF, SW>(v, buf);
+  cbar();
+  at_barrier();
+  lds_round<PL, RT, SW>(v, buf);
+}
+
 // The same for psi and lambda together (one barrier).
-template <class PL, int RF, int RT, int SW>
+template <class PL, int RF, int RT, int SW, class F>
 __device__ __forceinline__ void xp_pair(float2 (&v)[PL::NREG], float2 (&w)[PL::NREG], float2 *bv,
-                                        float2 *bw) {
+                                        float2 *bw, F at_barrier) {
   sts_round<PL, RF, SW>(v, bv);
   sts_round<PL, RF, SW>(w, bw);
   cbar();
+  at_barrier();
   lds_round<PL, RT, SW>(v, bv);
   lds_round<PL, RT, SW>(w, bw);
 }
+
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
 
 // exp(-i g f) from the raw 32-bit cost word (int32 or float32).
 // exp(-i g f) from the raw 32-bit cost word; M = 2 / 3: digit tables with M
@@ -528,19 +550,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
     c.x4 = (int)(T >> midbits);
     return c;
   };
-  auto issue = [&](uint64_t T) {
+  // Phase passes that read the cost tile before their last barrier load the
+  // next tile's costs as soon as that barrier passes, the state later.
+  constexpr bool early_cost = PH && !RED;
+  auto issue = [&](uint64_t T, bool cost) {
     const TC c = coords(T);
-    mbar_expect_tx(full, (P.init_plus ? 0u : L.tile_bytes) + (need_cost ? L.cost_bytes : 0u));
+    mbar_expect_tx(full, (P.init_plus ? 0u : L.tile_bytes) + (cost ? L.cost_bytes : 0u));
     if (!P.init_plus) tma_load(buf, &P.map_psi, c, full);
-    if (need_cost) tma_load(base + L.cost_off, &P.map_cost, c, full);
+    if (cost) tma_load(base + L.cost_off, &P.map_cost, c, full);
+  };
+  auto cost_next = [&](uint64_t T) {
+    if (tid == 0 && T + gridDim.x < P.ntiles) {
+      mbar_add_tx(full, L.cost_bytes);
+      tma_load(base + L.cost_off, &P.map_cost, coords(T + gridDim.x), full);
+    }
   };
   // after the tile's last shared-memory read: the buffers go to the next load
   auto release = [&](uint64_t T) {
     cbar();
-    if (tid == 0 && T + gridDim.x < P.ntiles) issue(T + gridDim.x);
+    if (tid == 0 && T + gridDim.x < P.ntiles) issue(T + gridDim.x, need_cost && !early_cost);
   };
 
-  if (tid == 0 && blockIdx.x < P.ntiles) issue(blockIdx.x);
+  if (tid == 0 && blockIdx.x < P.ntiles) issue(blockIdx.x, need_cost);
 
   FF acc_e, acc_o;  // this thread's energy / overlap terms
   int i = 0;
@@ -583,17 +614,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
       if constexpr (H2) {
         rot_tw<EB>(v, P.s2.m[NR - 1], P.tau2, P.form2);
         if constexpr (NR == 3) {
-          xp<PL, 2, 1, SW>(v, buf);
+          if constexpr (early_cost)
+            xp_hook<PL, 2, 1, SW>(v, buf, [&] { cost_next(T); });
+          else
+            xp<PL, 2, 1, SW>(v, buf);
           rot_tw<EB>(v, P.s2.m[1], P.tau2, P.form2);
         }
-        xp<PL, 1, 0, SW>(v, buf);
+        if constexpr (NR == 3) {
+          xp<PL, 1, 0, SW>(v, buf);
+        } else if constexpr (early_cost) {
+          xp_hook<PL, 1, 0, SW>(v, buf, [&] { cost_next(T); });
+        } else {
+          xp<PL, 1, 0, SW>(v, buf);
+        }
         if constexpr (!RED) release(T);
         rot_tw<EB>(v, P.s2.m[0], P.tau2, P.form2);
       }
     } else {
       if constexpr (PH) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tab, P.scl_phase);
       rot_tw<EB>(v, P.s2.m[0], P.tau2, P.form2);
-      xp<PL, 0, 1, SW>(v, buf);
+      if constexpr (early_cost)
+        xp_hook<PL, 0, 1, SW>(v, buf, [&] { cost_next(T); });
+      else
+        xp<PL, 0, 1, SW>(v, buf);
       if constexpr (NR == 2 && !RED) release(T);
       rot_tw<EB>(v, P.s2.m[1], P.tau2, P.form2);
       if constexpr (NR == 3) {
@@ -696,19 +739,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
     c.x4 = (int)(T >> midbits);
     return c;
   };
-  auto issue = [&](uint64_t T) {
+  // Passes whose cost reads end before a later barrier (lambda = f psi in the
+  // first round; the phase of a pivot) load the next tile's costs at that
+  // barrier, the vectors later.
+  constexpr bool early_cost = (PH && H2 && !INIT) || (INIT && !PH);
+  auto issue = [&](uint64_t T, bool cost) {
     const TC c = coords(T);
-    mbar_expect_tx(full, L.tile_bytes + (INIT ? 0u : L.tile_bytes) + (need_cost ? L.cost_bytes : 0u));
+    mbar_expect_tx(full, L.tile_bytes + (INIT ? 0u : L.tile_bytes) + (cost ? L.cost_bytes : 0u));
     tma_load(bv, &P.map_psi, c, full);
     if (!INIT) tma_load(bw, &P.map_lam, c, full);
-    if (need_cost) tma_load(base + L.cost_off, &P.map_cost, c, full);
+    if (cost) tma_load(base + L.cost_off, &P.map_cost, c, full);
+  };
+  auto cost_next = [&](uint64_t T) {
+    if (tid == 0 && T + gridDim.x < P.ntiles) {
+      mbar_add_tx(full, L.cost_bytes);
+      tma_load(base + L.cost_off, &P.map_cost, coords(T + gridDim.x), full);
+    }
   };
   // after the tile's last shared-memory read: the buffers go to the next load
   auto release = [&](uint64_t T) {
     cbar();
-    if (tid == 0 && T + gridDim.x < P.ntiles) issue(T + gridDim.x);
+    if (tid == 0 && T + gridDim.x < P.ntiles) issue(T + gridDim.x, need_cost && !early_cost);
   };
-  if (tid == 0 && blockIdx.x < P.ntiles) issue(blockIdx.x);
+
+  if (tid == 0 && blockIdx.x < P.ntiles) issue(blockIdx.x, need_cost);
 
   FF acc1, accg, acc2;  // this thread's gradient terms
   int i = 0;
@@ -738,11 +792,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
     }
     float a1 = 0.f, ag = 0.f, a2 = 0.f;
     unrot_tw<EB>(v, w, P.s1.m[0], P.tau1, P.form1, P.w1[0], a1);
-    xp_pair<PL, 0, 1, SW>(v, w, bv, bw);
+    if constexpr (INIT && early_cost)
+      xp_pair<PL, 0, 1, SW>(v, w, bv, bw, [&] { cost_next(T); });
+    else
+      xp_pair<PL, 0, 1, SW>(v, w, bv, bw, NoHook());
     if constexpr (NR == 2 && !PH && !H2) release(T);
     unrot_tw<EB>(v, w, P.s1.m[1], P.tau1, P.form1, P.w1[1], a1);
     if constexpr (NR == 3) {
-      xp_pair<PL, 1, 2, SW>(v, w, bv, bw);
+      xp_pair<PL, 1, 2, SW>(v, w, bv, bw, NoHook());
       if constexpr (!PH && !H2) release(T);
       unrot_tw<EB>(v, w, P.s1.m[2], P.tau1, P.form1, P.w1[2], a1);
     }
@@ -760,10 +817,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
     if constexpr (H2) {
       unrot_tw<EB>(v, w, P.s2.m[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
       if constexpr (NR == 3) {
-        xp_pair<PL, 2, 1, SW>(v, w, bv, bw);
+        if constexpr (PH && early_cost)
+          xp_pair<PL, 2, 1, SW>(v, w, bv, bw, [&] { cost_next(T); });
+        else
+          xp_pair<PL, 2, 1, SW>(v, w, bv, bw, NoHook());
         unrot_tw<EB>(v, w, P.s2.m[1], P.tau2, P.form2, P.w2[1], a2);
+        xp_pair<PL, 1, 0, SW>(v, w, bv, bw, NoHook());
+      } else if constexpr (PH && early_cost) {
+        xp_pair<PL, 1, 0, SW>(v, w, bv, bw, [&] { cost_next(T); });
+      } else {
+        xp_pair<PL, 1, 0, SW>(v, w, bv, bw, NoHook());
       }
-      xp_pair<PL, 1, 0, SW>(v, w, bv, bw);
       release(T);
       unrot_tw<EB>(v, w, P.s2.m[0], P.tau2, P.form2, P.w2[0], a2);
     }
