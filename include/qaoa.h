@@ -57,7 +57,15 @@ typedef enum {
     QAOA_ERR_BUSY = 9           /* serving: queue full, retry later        */
 } qaoa_status;
 
-typedef enum { QAOA_COST_I32 = 0, QAOA_COST_F32 = 1, QAOA_COST_F64 = 2 } qaoa_cost_type;
+/* Cost vector element types.  QAOA_COST_U16 holds integer values 0..65535,
+ * the paper's compact LABS storage (Sec. 4.4: f < 2^16 for the problems it
+ * simulates); half the memory and HBM traffic of int32. */
+typedef enum {
+    QAOA_COST_I32 = 0,
+    QAOA_COST_F32 = 1,
+    QAOA_COST_F64 = 2,
+    QAOA_COST_U16 = 3
+} qaoa_cost_type;
 typedef enum { QAOA_C64 = 0, QAOA_C128 = 1 } qaoa_state_type;
 
 /*
@@ -75,9 +83,10 @@ typedef struct {
     double f_min;       /* min_x f[x]                                    */
     double f_max;       /* max_x f[x]                                    */
     uint64_t n_min;     /* number of x with f[x] == f_min (ground states) */
-    uint32_t step_log2; /* int32 costs: largest k with 2^k dividing every
-                           f[x] - f_min (LABS: 2); 0 for other cost types
-                           and for a constant vector.  0 is always valid. */
+    uint32_t step_log2; /* int32 / uint16 costs: largest k with 2^k
+                           dividing every f[x] - f_min (LABS: at least 2); 0
+                           for float costs and for a constant vector.  0 is
+                           always valid. */
     uint32_t reserved;  /* 0 */
 } qaoa_cost_stats;
 
@@ -126,7 +135,8 @@ qaoa_status qaoa_maxcut_terms(int n, const int32_t *edges, const double *w,
  *     rounded once to the output type; when every weight is a multiple of
  *     2^-e with sum |w_k| 2^e < 2^53 the sum is exact (order-independent).
  *     QAOA_COST_F32 takes at most 1024 terms.
- *   d_costs: device, 2^n elements of the cost type.
+ *   d_costs: device, 2^n elements of the cost type (not QAOA_COST_U16: build
+ *     int32, then qaoa_convert_costs).
  */
 qaoa_status qaoa_precompute_costs(int n, const qaoa_term *terms, size_t n_terms,
                                   qaoa_cost_type ct, void *d_costs,
@@ -138,6 +148,25 @@ qaoa_status qaoa_precompute_costs(int n, const qaoa_term *terms, size_t n_terms,
  * int32, exact; O(n) per x instead of O(n^2) terms.  n <= 32.
  */
 qaoa_status qaoa_labs_costs(int n, int32_t *d_costs, qaoa_stream_t stream);
+
+/*
+ * The same LABS values stored as uint16 (QAOA_COST_U16; Sec. 4.4 stores the
+ * precomputed diagonal this way, its maximum (n-1)n(2n-1)/6 being below 2^16
+ * for every n <= 32 taken here).  d_costs: device, 2^n uint16, 16-byte
+ * aligned.  n <= 32.  Asynchronous.
+ */
+qaoa_status qaoa_labs_costs_u16(int n, uint16_t *d_costs, qaoa_stream_t stream);
+
+/*
+ * Element-type conversion of a cost vector: int32 -> uint16 or uint16 ->
+ * int32 (no other pair).  stats: of the source vector (host; for int32 ->
+ * uint16 every value must lie in [0, 65535], else QAOA_ERR_OVERFLOW before any
+ * launch).  d_src, d_dst: device, 2^n elements each, 16-byte aligned, not
+ * overlapping.  The statistics of the result are the source's.  Asynchronous.
+ */
+qaoa_status qaoa_convert_costs(int n, const void *d_src, qaoa_cost_type src_ct,
+                               const qaoa_cost_stats *stats, void *d_dst,
+                               qaoa_cost_type dst_ct, qaoa_stream_t stream);
 
 /*
  * Weighted MaxCut cost vector directly from the edge list (Background):

@@ -15,8 +15,14 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqaoa.so")
-SOURCES = ["api.cu", "pass_kernels.cu", "small_kernels.cu", "cost_kernels.cu", "profile.cu",
-           "tma_kernels.cu", "noalloc.cu", "serve.cu"]
+# (source, object, extra flags): the TMA kernels are compiled once per cost
+# element width (4 bytes: int32 / float32; 2 bytes: uint16), in parallel.
+UNITS = [("api.cu", "api.o", []), ("pass_kernels.cu", "pass_kernels.o", []),
+         ("small_kernels.cu", "small_kernels.o", []), ("cost_kernels.cu", "cost_kernels.o", []),
+         ("profile.cu", "profile.o", []), ("tma_kernels.cu", "tma_kernels.o", []),
+         ("tma_kernels.cu", "tma_kernels_u16.o", ["-DQAOA_TMA_CW=2"]),
+         ("noalloc.cu", "noalloc.o", []), ("serve.cu", "serve.o", [])]
+SOURCES = sorted({u[0] for u in UNITS})
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -34,9 +40,10 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
-def _compile(src, verbose):
-    obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+def _compile(unit, verbose):
+    src, obj_name, extra = unit
+    obj = os.path.join(BUILD, obj_name)
+    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *extra,
            "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
@@ -66,8 +73,8 @@ def build(force=False, verbose=False):
             and os.path.getmtime(LIB) >= _deps()):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
+    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+        results = list(ex.map(lambda u: _compile(u, verbose), UNITS))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)

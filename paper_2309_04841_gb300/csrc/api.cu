@@ -95,8 +95,10 @@ int num_sms() {
 bool aligned16(const void *p) { return p && ((uintptr_t)p & 15u) == 0; }
 
 bool valid_cost_type(qaoa_cost_type ct) {
-  return ct == QAOA_COST_I32 || ct == QAOA_COST_F32 || ct == QAOA_COST_F64;
+  return ct == QAOA_COST_I32 || ct == QAOA_COST_F32 || ct == QAOA_COST_F64 || ct == QAOA_COST_U16;
 }
+
+bool integer_cost(qaoa_cost_type ct) { return ct == QAOA_COST_I32 || ct == QAOA_COST_U16; }
 
 bool valid_state_type(qaoa_state_type st) { return st == QAOA_C64 || st == QAOA_C128; }
 
@@ -146,7 +148,7 @@ void make_phase(PhaseData<Real> &ph, double g, qaoa_cost_type ct, const qaoa_cos
   using C2 = typename C2T<Real>::type;
   memset(&ph, 0, sizeof(ph));
   const double range = stats ? stats->f_max - stats->f_min : 1e300;
-  if (ct == QAOA_COST_I32 && stats && range >= 0 && range < 65536.0) {
+  if (integer_cost(ct) && stats && range >= 0 && range < 65536.0) {
     ph.mode = 0;
     ph.fmin = (int)stats->f_min;
     ph.nhi = (int)(range / 256.0) + 1;
@@ -179,7 +181,7 @@ void make_phase(PhaseDigits &ph, double g, qaoa_cost_type ct, const qaoa_cost_st
     ph.d[e] = make_float2((float)z.real(), (float)z.imag());
   };
   const double fmin = stats ? stats->f_min : 0.0, unit = std::ldexp(g, shift);
-  if (ct == QAOA_COST_I32 && stats && rr >= 0 && 64.0 + std::floor(rr / 64.0) + 1.0 <= kPhaseMaxEntries) {
+  if (integer_cost(ct) && stats && rr >= 0 && 64.0 + std::floor(rr / 64.0) + 1.0 <= kPhaseMaxEntries) {
     // two digits: D0[d & 63], D1[d >> 6] (D1 with exp(-i g fmin) and the scale)
     const int n1 = (int)std::floor(rr / 64.0) + 1;
     ph.mode = 0;
@@ -190,7 +192,7 @@ void make_phase(PhaseDigits &ph, double g, qaoa_cost_type ct, const qaoa_cost_st
     ph.nent = 64 + n1;
     for (int j = 0; j < 64; ++j) put(j, unit * j, false);
     for (int j = 0; j < n1; ++j) put(64 + j, g * fmin + unit * 64.0 * j, true);
-  } else if (ct == QAOA_COST_I32 && stats && rr >= 0 && rr < 32768.0) {
+  } else if (integer_cost(ct) && stats && rr >= 0 && rr < 32768.0) {
     // three 5-bit digits
     ph.mode = 0;
     ph.nd = 3;
@@ -305,7 +307,9 @@ SmallLayer<Real> small_layer(double gamma, double beta) {
 
 int cost_kind(qaoa_cost_type ct) { return (int)ct; }
 
-double cost_bytes(qaoa_cost_type ct) { return ct == QAOA_COST_F64 ? 8.0 : 4.0; }
+double cost_bytes(qaoa_cost_type ct) {
+  return ct == QAOA_COST_F64 ? 8.0 : ct == QAOA_COST_U16 ? 2.0 : 4.0;
+}
 
 // ----------------------------------------------------------- small path
 
@@ -567,14 +571,14 @@ qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qao
 
 // ---------------------------------------------------- TMA (complex64) path
 
-bool tma_ok(qaoa_cost_type ct) { return ct == QAOA_COST_I32 || ct == QAOA_COST_F32; }
+bool tma_ok(qaoa_cost_type ct) { return ct == QAOA_COST_I32 || ct == QAOA_COST_F32 || ct == QAOA_COST_U16; }
 
 // Reduced ("tan") form of exp(-i b X) (forward) or exp(+i b X) (adjoint):
 // exp(-/+ i b X) = sigma * G with |tau| <= 1 (see TmaFwdParams).
 // f_min as the 32-bit word the cost vector holds (int32 or float32 bits).
 uint32_t fmin_word(qaoa_cost_type ct, const qaoa_cost_stats *stats) {
   const double f = stats ? stats->f_min : 0.0;
-  if (ct == QAOA_COST_I32) return (uint32_t)(int32_t)f;
+  if (integer_cost(ct)) return (uint32_t)(int32_t)f;
   const float x = (float)f;
   uint32_t w;
   memcpy(&w, &x, sizeof(w));
@@ -631,7 +635,8 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
     const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
     CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, 128), "tensor map (state)");
     P.psi = reinterpret_cast<float2 *>(state);
-    CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, 4, 0), "tensor map (cost)");
+    CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, (int)cost_bytes(ct), 0),
+       "tensor map (cost)");
     P.ntiles = 1ull << (n - TB);
     P.h = h;
     P.c = c;
@@ -676,9 +681,10 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
     P.out = d_out;
     P.err = ws.err;
     const double N = (double)(1ull << n);
-    const double bytes = (P.init_plus ? 8.0 : 16.0) * N + ((P.has_phase || P.reduce) ? 4.0 * N : 0.0);
+    const double bytes = (P.init_plus ? 8.0 : 16.0) * N + ((P.has_phase || P.reduce) ? cost_bytes(ct) * N : 0.0);
     const int kind = (op.l1 >= 0 ? 1 : 0) | (P.has_phase ? 2 : 0) | (op.l2 >= 0 ? 4 : 0) | (P.reduce ? 8 : 0);
-    LAUNCH_N(tma_pass_name(true, G.high, kind), bytes, s, launch_fwd_tma(P, G.high, s, nsm));
+    LAUNCH_N(tma_pass_name(true, G.high, kind), bytes, s,
+             ct == QAOA_COST_U16 ? launch_fwd_tma_u16(P, G.high, s, nsm) : launch_fwd_tma(P, G.high, s, nsm));
   }
   return QAOA_OK;
 }
@@ -707,7 +713,8 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     CK(make_tile_map(&P.map_lam, lam, n, TB, h, c, 8, sw), "tensor map (lambda)");
     P.psi = reinterpret_cast<float2 *>(state);
     P.lam = reinterpret_cast<float2 *>(lam);
-    CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, 4, 0), "tensor map (cost)");
+    CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, (int)cost_bytes(ct), 0),
+       "tensor map (cost)");
     P.ntiles = 1ull << (n - TB);
     P.h = h;
     P.c = c;
@@ -753,9 +760,11 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     P.counter = ws.counter;
     P.err = ws.err;
     const double N = (double)(1ull << n);
-    const double bytes = (P.init_lambda ? 24.0 : 32.0) * N + ((P.has_phase || P.init_lambda) ? 4.0 * N : 0.0);
+    const double bytes =
+        (P.init_lambda ? 24.0 : 32.0) * N + ((P.has_phase || P.init_lambda) ? cost_bytes(ct) * N : 0.0);
     const int kind = (P.has_phase ? 2 : 0) | (op.l2 >= 0 ? 4 : 0) | (P.init_lambda ? 8 : 0);
-    LAUNCH_N(tma_pass_name(false, G.high, kind), bytes, s, launch_bwd_tma(P, G.high, s, nsm));
+    LAUNCH_N(tma_pass_name(false, G.high, kind), bytes, s,
+             ct == QAOA_COST_U16 ? launch_bwd_tma_u16(P, G.high, s, nsm) : launch_bwd_tma(P, G.high, s, nsm));
   }
   return QAOA_OK;
 }
@@ -900,6 +909,8 @@ qaoa_status qaoa_precompute_costs(int n, const qaoa_term *terms, size_t n_terms,
                                   void *d_costs, qaoa_stream_t stream) {
   if (n < 1 || n > QAOA_MAX_N) return fail(QAOA_ERR_INVALID_ARG, "n out of range");
   if (!valid_cost_type(ct) || !aligned16(d_costs)) return fail(QAOA_ERR_INVALID_ARG, "bad cost type or pointer");
+  if (ct == QAOA_COST_U16)
+    return fail(QAOA_ERR_INVALID_ARG, "precompute_costs: build int32 costs, then qaoa_convert_costs to uint16");
   if (n_terms && !terms) return fail(QAOA_ERR_INVALID_ARG, "NULL terms");
   const uint64_t lim = n == 64 ? ~0ull : ((1ull << n) - 1ull);
   std::vector<double> w(n_terms);
@@ -966,10 +977,35 @@ qaoa_status qaoa_labs_costs(int n, int32_t *d_costs, qaoa_stream_t stream) {
   return QAOA_OK;
 }
 
+qaoa_status qaoa_labs_costs_u16(int n, uint16_t *d_costs, qaoa_stream_t stream) {
+  if (n < 2 || n > 32) return fail(QAOA_ERR_INVALID_ARG, "labs_costs_u16: n must be in [2, 32]");
+  if (!aligned16(d_costs)) return fail(QAOA_ERR_INVALID_ARG, "labs_costs_u16: bad pointer");
+  // max f = (n-1) n (2n-1) / 6 (all spins equal) < 2^16 for every n <= 32
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  LAUNCH("costs_labs", 2.0 * (double)(1ull << n), s, launch_labs_u16(n, d_costs, s, num_sms()));
+  return QAOA_OK;
+}
+
+qaoa_status qaoa_convert_costs(int n, const void *d_src, qaoa_cost_type src_ct,
+                               const qaoa_cost_stats *stats, void *d_dst, qaoa_cost_type dst_ct,
+                               qaoa_stream_t stream) {
+  if (n < 1 || n > QAOA_MAX_N || !aligned16(d_src) || !aligned16(d_dst) || !stats)
+    return fail(QAOA_ERR_INVALID_ARG, "convert_costs: bad n, pointer or NULL stats");
+  const bool to16 = src_ct == QAOA_COST_I32 && dst_ct == QAOA_COST_U16;
+  const bool from16 = src_ct == QAOA_COST_U16 && dst_ct == QAOA_COST_I32;
+  if (!to16 && !from16) return fail(QAOA_ERR_INVALID_ARG, "convert_costs: only int32 <-> uint16");
+  if (to16 && !(stats->f_min >= 0.0 && stats->f_max <= 65535.0))
+    return fail(QAOA_ERR_OVERFLOW, "convert_costs: values outside [0, 65535] (stats of the int32 vector)");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  LAUNCH("costs_convert", (cost_bytes(src_ct) + cost_bytes(dst_ct)) * (double)(1ull << n), s,
+         launch_convert(n, d_src, cost_kind(src_ct), d_dst, cost_kind(dst_ct), s, num_sms()));
+  return QAOA_OK;
+}
+
 qaoa_status qaoa_maxcut_costs(int n, const int32_t *edges, const double *w, size_t m,
                               qaoa_cost_type ct, void *d_costs, qaoa_stream_t stream) {
-  if (n < 2 || n > QAOA_MAX_N || !valid_cost_type(ct) || !aligned16(d_costs))
-    return fail(QAOA_ERR_INVALID_ARG, "maxcut_costs: bad n, type or pointer");
+  if (n < 2 || n > QAOA_MAX_N || !valid_cost_type(ct) || ct == QAOA_COST_U16 || !aligned16(d_costs))
+    return fail(QAOA_ERR_INVALID_ARG, "maxcut_costs: bad n, type or pointer (uint16: convert from int32)");
   if (m > (size_t)kEdgeMax || (m && !edges)) return fail(QAOA_ERR_INVALID_ARG, "maxcut_costs: too many edges or NULL");
   std::vector<double> wv(m);
   for (size_t e = 0; e < m; ++e) {

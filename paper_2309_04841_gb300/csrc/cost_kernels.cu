@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(256) k_terms(const __grid_constant__ TermChunk
 
 // LABS: f(x) = sum_{k=1}^{n-1} C_k^2, C_k = (n - k) - 2 popc((x ^ x >> k) & (2^{n-k} - 1)):
 // the aperiodic autocorrelation counts agreeing minus disagreeing pairs.
-__global__ void __launch_bounds__(256) k_labs(int n, int32_t *out) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_labs(int n, T *out) {
   const uint64_t N = 1ull << n;
   for (uint64_t x = blockIdx.x * 256ull + threadIdx.x; x < N; x += (uint64_t)gridDim.x * 256ull) {
     const uint32_t xi = (uint32_t)x;
@@ -72,8 +73,16 @@ __global__ void __launch_bounds__(256) k_labs(int n, int32_t *out) {
       const int32_t c = (n - k) - 2 * __popc((xi ^ (xi >> k)) & m);
       f += c * c;
     }
-    out[x] = f;
+    out[x] = (T)f;
   }
+}
+
+// Element type conversion of a cost vector (int32 <-> uint16; the host has
+// checked that every value fits the destination).
+template <typename S, typename D>
+__global__ void __launch_bounds__(256) k_convert(uint64_t N, const S *src, D *dst) {
+  for (uint64_t x = blockIdx.x * 256ull + threadIdx.x; x < N; x += (uint64_t)gridDim.x * 256ull)
+    dst[x] = (D)__ldg(src + x);
 }
 
 // MaxCut: f(x) = -sum_{(i,j) cut by x} w_ij, accumulated in edge order.
@@ -112,6 +121,7 @@ __global__ void __launch_bounds__(256) k_maxcut(const __grid_constant__ EdgeChun
 
 __device__ __forceinline__ double cost_at(const void *cost, int kind, uint64_t x) {
   if (kind == kCostI32) return (double)__ldg(reinterpret_cast<const int *>(cost) + x);
+  if (kind == kCostU16) return (double)__ldg(reinterpret_cast<const unsigned short *>(cost) + x);
   if (kind == kCostF32) return (double)__ldg(reinterpret_cast<const float *>(cost) + x);
   return __ldg(reinterpret_cast<const double *>(cost) + x);
 }
@@ -139,12 +149,14 @@ __global__ void __launch_bounds__(256) k_cost_stats(int n, const void *cost, int
   MinMaxCnt a = {INFINITY, -INFINITY, 0.0};
   uint32_t bits = 0u;
   const int *ci = reinterpret_cast<const int *>(cost);
-  const int f0 = kind == kCostI32 ? __ldg(ci) : 0;
+  const unsigned short *cu = reinterpret_cast<const unsigned short *>(cost);
+  const int f0 = kind == kCostI32 ? __ldg(ci) : kind == kCostU16 ? (int)__ldg(cu) : 0;
   for (uint64_t x = blockIdx.x * 256ull + threadIdx.x; x < N; x += (uint64_t)gridDim.x * 256ull) {
     const double f = cost_at(cost, kind, x);
     MinMaxCnt b = {f, f, 1.0};
     a = mmc_join(a, b);
     if (kind == kCostI32) bits |= (uint32_t)(__ldg(ci + x) - f0);
+    if (kind == kCostU16) bits |= (uint32_t)((int)__ldg(cu + x) - f0);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -264,7 +276,26 @@ cudaError_t launch_terms(const TermChunk &P, cudaStream_t s, int nsm) {
 }
 
 cudaError_t launch_labs(int n, int32_t *out, cudaStream_t s, int nsm) {
-  k_labs<<<grid_for(n, nsm, 8), 256, 0, s>>>(n, out);
+  k_labs<int32_t><<<grid_for(n, nsm, 8), 256, 0, s>>>(n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_labs_u16(int n, uint16_t *out, cudaStream_t s, int nsm) {
+  k_labs<uint16_t><<<grid_for(n, nsm, 8), 256, 0, s>>>(n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int n, const void *src, int src_kind, void *dst, int dst_kind,
+                           cudaStream_t s, int nsm) {
+  const uint64_t N = 1ull << n;
+  if (src_kind == kCostI32 && dst_kind == kCostU16)
+    k_convert<int32_t, uint16_t><<<grid_for(n, nsm, 8), 256, 0, s>>>(
+        N, reinterpret_cast<const int32_t *>(src), reinterpret_cast<uint16_t *>(dst));
+  else if (src_kind == kCostU16 && dst_kind == kCostI32)
+    k_convert<uint16_t, int32_t><<<grid_for(n, nsm, 8), 256, 0, s>>>(
+        N, reinterpret_cast<const uint16_t *>(src), reinterpret_cast<int32_t *>(dst));
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

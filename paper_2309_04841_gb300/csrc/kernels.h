@@ -36,6 +36,9 @@ struct EdgeChunk {
 
 cudaError_t launch_terms(const TermChunk &P, cudaStream_t s, int nsm);
 cudaError_t launch_labs(int n, int32_t *out, cudaStream_t s, int nsm);
+cudaError_t launch_labs_u16(int n, uint16_t *out, cudaStream_t s, int nsm);
+cudaError_t launch_convert(int n, const void *src, int src_kind, void *dst, int dst_kind,
+                           cudaStream_t s, int nsm);
 cudaError_t launch_maxcut(const EdgeChunk &P, cudaStream_t s, int nsm);
 unsigned reduce_grid(int n, int nsm);
 cudaError_t launch_cost_stats(int n, const void *cost, int kind, double *partials,
@@ -145,8 +148,11 @@ struct alignas(64) TmaBwdParams {
 
 cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, int c, int esz,
                           int swizzle_bytes);
+// TMA passes over 4-byte (int32 / float32) and 2-byte (uint16) cost vectors.
 cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm);
 cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm);
+cudaError_t launch_fwd_tma_u16(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm);
+cudaError_t launch_bwd_tma_u16(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm);
 
 cudaError_t launch_small_batch(const SmallJob<float> *d_jobs, int count, int max_n, cudaStream_t s);
 cudaError_t launch_small_batch(const SmallJob<double> *d_jobs, int count, int max_n, cudaStream_t s);

@@ -144,6 +144,9 @@ __device__ __forceinline__ void cost_split(const void *cost, int kind, uint64_t 
     const int f = __ldg(reinterpret_cast<const int *>(cost) + x);
     hi = (float)f;
     lo = (float)((long long)f - (long long)hi);
+  } else if (kind == kCostU16) {
+    hi = (float)__ldg(reinterpret_cast<const unsigned short *>(cost) + x);
+    lo = 0.f;
   } else if (kind == kCostF32) {
     hi = __ldg(reinterpret_cast<const float *>(cost) + x);
     lo = 0.f;
@@ -156,6 +159,7 @@ __device__ __forceinline__ void cost_split(const void *cost, int kind, uint64_t 
 
 __device__ __forceinline__ double cost_d(const void *cost, int kind, uint64_t x) {
   if (kind == kCostI32) return (double)__ldg(reinterpret_cast<const int *>(cost) + x);
+  if (kind == kCostU16) return (double)__ldg(reinterpret_cast<const unsigned short *>(cost) + x);
   if (kind == kCostF32) return (double)__ldg(reinterpret_cast<const float *>(cost) + x);
   return __ldg(reinterpret_cast<const double *>(cost) + x);
 }
@@ -165,7 +169,8 @@ __device__ __forceinline__ float2 phase_factor(const PhaseData<float> &ph, const
                                                const float2 *thi, const void *cost, int kind,
                                                uint64_t x) {
   if (ph.mode == 0) {
-    const int f = __ldg(reinterpret_cast<const int *>(cost) + x);
+    const int f = kind == kCostU16 ? (int)__ldg(reinterpret_cast<const unsigned short *>(cost) + x)
+                                   : __ldg(reinterpret_cast<const int *>(cost) + x);
     const uint32_t v = (uint32_t)(f - ph.fmin);
     const uint32_t hi = min(v >> 8, 255u);
     return cmul(thi[hi], tlo[v & 255u]);
@@ -187,7 +192,8 @@ __device__ __forceinline__ double2 phase_factor(const PhaseData<double> &ph, con
                                                 const double2 *thi, const void *cost, int kind,
                                                 uint64_t x) {
   if (ph.mode == 0) {
-    const int f = __ldg(reinterpret_cast<const int *>(cost) + x);
+    const int f = kind == kCostU16 ? (int)__ldg(reinterpret_cast<const unsigned short *>(cost) + x)
+                                   : __ldg(reinterpret_cast<const int *>(cost) + x);
     const uint32_t v = (uint32_t)(f - ph.fmin);
     const uint32_t hi = min(v >> 8, 255u);
     return cmul(thi[hi], tlo[v & 255u]);

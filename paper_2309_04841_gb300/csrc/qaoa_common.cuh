@@ -94,7 +94,7 @@ static_assert(PlanT11Low::valid() && PlanT11High::valid(), "bad T11 plan");
 // (128 B for complex64, 256 B for complex128) per global segment.
 constexpr int kHighC = 4;
 
-enum CostKind : int { kCostI32 = 0, kCostF32 = 1, kCostF64 = 2 };
+enum CostKind : int { kCostI32 = 0, kCostF32 = 1, kCostF64 = 2, kCostU16 = 3 };
 
 // Tile geometry of one pass (see file comment).
 struct Geom {

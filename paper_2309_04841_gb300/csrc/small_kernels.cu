@@ -27,6 +27,7 @@ __device__ __forceinline__ C2 cm(C2 a, C2 b) {
 
 __device__ __forceinline__ double ld_cost(const void *cost, int kind, int x) {
   if (kind == kCostI32) return (double)reinterpret_cast<const int *>(cost)[x];
+  if (kind == kCostU16) return (double)reinterpret_cast<const unsigned short *>(cost)[x];
   if (kind == kCostF32) return (double)reinterpret_cast<const float *>(cost)[x];
   return reinterpret_cast<const double *>(cost)[x];
 }
@@ -39,6 +40,9 @@ __device__ __forceinline__ float2 small_phase(const SmallLayer<float> &L, const 
     const int f = reinterpret_cast<const int *>(cost)[x];
     fh = (float)f;
     fl = (float)((long long)f - (long long)fh);
+  } else if (kind == kCostU16) {
+    fh = (float)reinterpret_cast<const unsigned short *>(cost)[x];
+    fl = 0.f;
   } else if (kind == kCostF32) {
     fh = reinterpret_cast<const float *>(cost)[x];
     fl = 0.f;

@@ -18,12 +18,23 @@
 // on timeout the kernel records an error word and returns.
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "qaoa_common.cuh"
 #include "kernels.h"
+
+// Cost vector element width of this compilation: 4 (int32 / float32) or 2
+// (uint16).  The build compiles this file once for each.
+#ifndef QAOA_TMA_CW
+#define QAOA_TMA_CW 4
+#endif
 
 namespace qaoa {
 
 namespace {
+
+using CostWord = std::conditional_t<QAOA_TMA_CW == 2, uint16_t, uint32_t>;
+constexpr uint32_t kCW = QAOA_TMA_CW;
 
 constexpr uint64_t kWaitNs = 1000000000ull;  // bounded waits: 1 s
 
@@ -295,7 +306,7 @@ __device__ __forceinline__ float2 phase_of(const PhaseDigits &ph, int kind, cons
     }
   } else {
     float fh, fl;
-    if (kind == kCostI32) {
+    if (kind != kCostF32) {  // int32 or uint16
       const int f = (int)word;
       fh = (float)f;
       fl = (float)((long long)f - (long long)fh);
@@ -327,12 +338,12 @@ __device__ __forceinline__ void fill_phase_tab(float2 *tab, const PhaseDigits &p
 }
 
 __device__ __forceinline__ float cost_val(int kind, uint32_t word) {
-  return kind == kCostI32 ? (float)(int)word : __uint_as_float(word);
+  return kind == kCostF32 ? __uint_as_float(word) : (float)(int)word;
 }
 
 // v <- v * exp(-i g f) (* scl in computed mode; table mode has it folded in).
 template <class PL, int R, int M>
-__device__ __forceinline__ void phase_round_m(float2 (&v)[PL::NREG], const uint32_t *cb,
+__device__ __forceinline__ void phase_round_m(float2 (&v)[PL::NREG], const CostWord *cb,
                                               const PhaseDigits &ph, int kind, const float2 *tab,
                                               float2 scl) {
   const uint32_t tt = thr_tile<PL, R>();
@@ -344,7 +355,7 @@ __device__ __forceinline__ void phase_round_m(float2 (&v)[PL::NREG], const uint3
 }
 
 template <class PL, int R>
-__device__ __forceinline__ void phase_round(float2 (&v)[PL::NREG], const uint32_t *cb,
+__device__ __forceinline__ void phase_round(float2 (&v)[PL::NREG], const CostWord *cb,
                                             const PhaseDigits &ph, int kind, const float2 *tab,
                                             float2 scl) {
   const int m = phase_m(ph);
@@ -369,9 +380,9 @@ struct FF {
 };
 
 template <class PL, int R>
-__device__ __forceinline__ void eo_round(const float2 (&v)[PL::NREG], const uint32_t *cb, int kind,
+__device__ __forceinline__ void eo_round(const float2 (&v)[PL::NREG], const CostWord *cb, int kind,
                                          uint32_t fmin_word, float &e, float &o) {
-  // f == f_min is tested on the raw 32-bit words (exact for int32 costs; for
+  // f == f_min is tested on the raw words (exact for integer costs; for
   // float32 costs f_min is one of the stored values, and +0 / -0 compare equal)
   const uint32_t tt = thr_tile<PL, R>();
 #pragma unroll
@@ -380,7 +391,7 @@ __device__ __forceinline__ void eo_round(const float2 (&v)[PL::NREG], const uint
     const float f = cost_val(kind, w);
     const float pr = v[r].x * v[r].x + v[r].y * v[r].y;
     e += pr * f;
-    const bool at_min = kind == kCostI32 ? w == fmin_word : f == __uint_as_float(fmin_word);
+    const bool at_min = kind != kCostF32 ? w == fmin_word : f == __uint_as_float(fmin_word);
     o += at_min ? pr : 0.f;
   }
 }
@@ -444,7 +455,7 @@ __device__ __forceinline__ Lay layout(uint32_t tile_elems, bool two, bool cost) 
   L.tile_bytes = tile_elems * 8u;
   L.lam_off = L.tile_bytes;
   L.cost_off = L.lam_off + (two ? L.tile_bytes : 0u);
-  L.cost_bytes = cost ? tile_elems * 4u : 0u;
+  L.cost_bytes = cost ? tile_elems * kCW : 0u;
   L.tab_off = L.cost_off + L.cost_bytes;
   L.bar_off = L.tab_off + (uint32_t)kPhaseTabEntries * 8u;
   L.red_off = L.bar_off + 32u;
@@ -485,9 +496,9 @@ __device__ __forceinline__ unsigned char *aligned_base(unsigned char *raw) {
 
 }  // namespace
 
-size_t tma_smem_bytes(int tb, bool two, bool cost) {
+static size_t smem_bytes(int tb, bool two, bool cost) {
   const size_t te = (size_t)1 << tb;
-  return 1024 + te * 8 * (two ? 2 : 1) + (cost ? te * 4 : 0) + kPhaseTabEntries * 8 + 32 + 8 * 3 * 8;
+  return 1024 + te * 8 * (two ? 2 : 1) + (cost ? te * kCW : 0) + kPhaseTabEntries * 8 + 32 + 8 * 3 * 8;
 }
 
 // ------------------------------------------------------------- forward
@@ -524,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
   unsigned char *base = aligned_base(smem_raw);
   const Lay L = layout(1u << PL::TB, false, need_cost);
   float2 *buf = reinterpret_cast<float2 *>(base);
-  const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off);
+  const CostWord *cb = reinterpret_cast<const CostWord *>(base + L.cost_off);
   float2 *tab = reinterpret_cast<float2 *>(base + L.tab_off);
   uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off);
   double *red = reinterpret_cast<double *>(base + L.red_off);
@@ -687,7 +698,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
 // lambda times the un-phase factor exp(+i g f) (phase mode M as in phase_of).
 template <class PL, int R, int M>
 __device__ __forceinline__ void unphase_round(float2 (&v)[PL::NREG], float2 (&w)[PL::NREG],
-                                              const uint32_t *cb, const TmaBwdParams &P,
+                                              const CostWord *cb, const TmaBwdParams &P,
                                               const float2 *tab, float &ag) {
   const uint32_t tt = thr_tile<PL, R>();
 #pragma unroll
@@ -713,7 +724,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
   const Lay L = layout(1u << PL::TB, true, need_cost);
   float2 *bv = reinterpret_cast<float2 *>(base);
   float2 *bw = reinterpret_cast<float2 *>(base + L.lam_off);
-  const uint32_t *cb = reinterpret_cast<const uint32_t *>(base + L.cost_off);
+  const CostWord *cb = reinterpret_cast<const CostWord *>(base + L.cost_off);
   float2 *tab = reinterpret_cast<float2 *>(base + L.tab_off);
   uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off);
   double *red = reinterpret_cast<double *>(base + L.red_off);
@@ -861,6 +872,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
 
 // ---------------------------------------------------------------- host side
 
+// Shared by both cost widths: defined in the 4-byte compilation only.
+#if QAOA_TMA_CW == 4
 namespace {
 
 using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -915,7 +928,9 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
     for (int i = 0; i < 4; ++i) strides[i] = st[i];
   }
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  const CUtensorMapDataType dt = esz == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+  const CUtensorMapDataType dt = esz == 8   ? CU_TENSOR_MAP_DATA_TYPE_UINT64
+                                 : esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                            : CU_TENSOR_MAP_DATA_TYPE_UINT32;
   const CUtensorMapSwizzle sw = swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                                 : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                                       : CU_TENSOR_MAP_SWIZZLE_NONE;
@@ -923,14 +938,15 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+#endif  // QAOA_TMA_CW == 4
 
 template <class PL, int K>
 static cudaError_t launch_fwd_tma_t(const TmaFwdParams &P, cudaStream_t s, int nsm) {
-  const size_t smem = tma_smem_bytes(PL::TB, false, (K & (kPH | kRED)) != 0);
+  const size_t smem = smem_bytes(PL::TB, false, (K & (kPH | kRED)) != 0);
   auto kern = k_fwd_tma<PL, K>;
   static int nb = 0;
   if (nb == 0) {
-    const size_t mx = tma_smem_bytes(PL::TB, false, true);
+    const size_t mx = smem_bytes(PL::TB, false, true);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e != cudaSuccess) return e;
     int b = 0;
@@ -945,11 +961,11 @@ static cudaError_t launch_fwd_tma_t(const TmaFwdParams &P, cudaStream_t s, int n
 
 template <class PL, int K>
 static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int nsm) {
-  const size_t smem = tma_smem_bytes(PL::TB, true, (K & (kPH | kINIT)) != 0);
+  const size_t smem = smem_bytes(PL::TB, true, (K & (kPH | kINIT)) != 0);
   auto kern = k_bwd_tma<PL, K>;
   static int nb = 0;
   if (nb == 0) {
-    const size_t mx = tma_smem_bytes(PL::TB, true, true);
+    const size_t mx = smem_bytes(PL::TB, true, true);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e != cudaSuccess) return e;
     int b = 0;
@@ -992,13 +1008,19 @@ static cudaError_t dispatch_bwd(const TmaBwdParams &P, cudaStream_t s, int nsm) 
   }
 }
 
-cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm) {
+#if QAOA_TMA_CW == 2
+#define QAOA_TMA_FN(name) name##_u16
+#else
+#define QAOA_TMA_FN(name) name
+#endif
+
+cudaError_t QAOA_TMA_FN(launch_fwd_tma)(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm) {
   if (P.c != 4 && P.c != 5) return cudaErrorInvalidValue;  // 16- or 32-amplitude segments
   if (!P.psi || ((uintptr_t)P.psi & 15u)) return cudaErrorInvalidValue;
   return high ? dispatch_fwd<PlanTmaF13High>(P, s, nsm) : dispatch_fwd<PlanTmaF13Low>(P, s, nsm);
 }
 
-cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {
+cudaError_t QAOA_TMA_FN(launch_bwd_tma)(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {
   if (P.c != 4 && P.c != 5) return cudaErrorInvalidValue;  // 16- or 32-amplitude segments
   if (!P.psi || !P.lam || ((uintptr_t)P.psi & 15u) || ((uintptr_t)P.lam & 15u))
     return cudaErrorInvalidValue;

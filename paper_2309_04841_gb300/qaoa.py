@@ -13,7 +13,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libqaoa.so")
 
-COST_I32, COST_F32, COST_F64 = 0, 1, 2
+COST_I32, COST_F32, COST_F64, COST_U16 = 0, 1, 2, 3
 C64, C128 = 0, 1
 
 TERM_DTYPE = np.dtype([("weight", np.float64), ("mask", np.uint64)])
@@ -89,6 +89,8 @@ def lib():
             "qaoa_maxcut_terms": ([I, P, P, Z, P, Z, P], I),
             "qaoa_precompute_costs": ([I, P, Z, I, P, P], I),
             "qaoa_labs_costs": ([I, P, P], I),
+            "qaoa_labs_costs_u16": ([I, P, P], I),
+            "qaoa_convert_costs": ([I, P, I, P, P, I, P], I),
             "qaoa_maxcut_costs": ([I, P, P, Z, I, P, P], I),
             "qaoa_cost_stats_compute": ([I, P, I, P, Z, P, P], I),
             "qaoa_simulate": ([I, P, I, P, P, P, I, P, I, I, P, Z, P, P], I),
@@ -138,8 +140,11 @@ def _np_ptr(a):
 
 
 def cost_dtype(ct):
+    """torch dtype holding a cost vector of type ct (uint16 costs live in an
+    int16 tensor; the library reads its bits as unsigned)."""
     torch = _torch()
-    return {COST_I32: torch.int32, COST_F32: torch.float32, COST_F64: torch.float64}[ct]
+    return {COST_I32: torch.int32, COST_F32: torch.float32, COST_F64: torch.float64,
+            COST_U16: torch.int16}[ct]
 
 
 def state_dtype(st):
@@ -149,7 +154,11 @@ def state_dtype(st):
 
 def cost_type_of(costs):
     torch = _torch()
-    return {torch.int32: COST_I32, torch.float32: COST_F32, torch.float64: COST_F64}[costs.dtype]
+    m = {torch.int32: COST_I32, torch.float32: COST_F32, torch.float64: COST_F64,
+         torch.int16: COST_U16}
+    if hasattr(torch, "uint16"):
+        m[torch.uint16] = COST_U16
+    return m[costs.dtype]
 
 
 def state_type_of(state):
@@ -230,6 +239,26 @@ def labs_costs(n, out=None):
     if out is None:
         out = torch.empty(1 << n, dtype=torch.int32, device="cuda")
     _check(lib().qaoa_labs_costs(n, _ptr(out), _stream()))
+    return out
+
+
+def labs_costs_u16(n, out=None):
+    """LABS costs as uint16 (in an int16 tensor; see cost_dtype)."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(1 << n, dtype=torch.int16, device="cuda")
+    _check(lib().qaoa_labs_costs_u16(n, _ptr(out), _stream()))
+    return out
+
+
+def convert_costs(costs, stats, cost_type=COST_U16, out=None):
+    """int32 <-> uint16 copy of a cost vector (stats: those of `costs`)."""
+    torch = _torch()
+    n = _n_of(costs)
+    if out is None:
+        out = torch.empty(1 << n, dtype=cost_dtype(cost_type), device=costs.device)
+    _check(lib().qaoa_convert_costs(n, _ptr(costs), cost_type_of(costs), C.byref(stats), _ptr(out),
+                                    cost_type, _stream()))
     return out
 
 

@@ -144,3 +144,21 @@ def test_server_validation_without_gpu(L):
     cfg = Q.ServerConfig(4, 10, 10)
     assert L.qaoa_server_create(C.byref(cfg), C.c_void_p(100), 1 << 30, C.byref(h)) == 1  # alignment
     assert L.qaoa_server_submit(None, None, None) == 1
+
+
+def test_u16_validation_without_gpu(L):
+    # uint16 costs: builders and conversion check their arguments before any launch
+    P = C.c_void_p
+    assert L.qaoa_labs_costs_u16(33, P(256), None) == 1  # n > 32
+    assert L.qaoa_labs_costs_u16(10, P(258), None) == 1  # misaligned
+    t = Q.terms_array([(1.0, (0,))])
+    assert L.qaoa_precompute_costs(4, Q._np_ptr(t), 1, Q.COST_U16, P(256), None) == 1
+    e = np.array([[0, 1]], dtype=np.int32)
+    assert L.qaoa_maxcut_costs(4, Q._np_ptr(e), None, 1, Q.COST_U16, P(256), None) == 1
+    neg = Q.CostStats(-3.0, 5.0, 1)
+    assert L.qaoa_convert_costs(4, P(256), Q.COST_I32, C.byref(neg), P(512), Q.COST_U16, None) == 3
+    big = Q.CostStats(0.0, 70000.0, 1)
+    assert L.qaoa_convert_costs(4, P(256), Q.COST_I32, C.byref(big), P(512), Q.COST_U16, None) == 3
+    ok = Q.CostStats(0.0, 5.0, 1)
+    assert L.qaoa_convert_costs(4, P(256), Q.COST_F32, C.byref(ok), P(512), Q.COST_U16, None) == 1
+    assert L.qaoa_convert_costs(4, P(256), Q.COST_I32, None, P(512), Q.COST_U16, None) == 1
