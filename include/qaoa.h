@@ -264,6 +264,16 @@ qaoa_status qaoa_simulate_noalloc(int n, const void *d_costs, qaoa_cost_type ct,
 /* ---------------------------------------------------- a5: reductions */
 
 /*
+ * Probabilities |psi_x|^2 of the state in d_state (Sec. 4, get_probabilities).
+ *   d_probs: device, 2^n reals (float for QAOA_C64, double for QAOA_C128),
+ *     16-byte aligned; or NULL for in place: every amplitude of d_state is
+ *     replaced by |psi_x|^2 + 0i (the paper's preserve_state = False).
+ * Asynchronous.
+ */
+qaoa_status qaoa_probabilities(int n, void *d_state, qaoa_state_type st, void *d_probs,
+                               qaoa_stream_t stream);
+
+/*
  * Expectation sum_x |psi_x|^2 f_x (Sec. 3.1) of the state in d_state, written
  * to d_out[0] (device double).  Deterministic order.  Asynchronous.
  */

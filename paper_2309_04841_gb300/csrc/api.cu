@@ -1098,6 +1098,18 @@ qaoa_status qaoa_simulate(int n, const void *d_costs, qaoa_cost_type ct, const q
              : tiled_forward<double>(n, d_costs, ct, stats, gammas, betas, p, d_state, init_plus, ws, d_out, s);
 }
 
+qaoa_status qaoa_probabilities(int n, void *d_state, qaoa_state_type st, void *d_probs,
+                               qaoa_stream_t stream) {
+  if (n < 1 || n > QAOA_MAX_N || !valid_state_type(st) || !aligned16(d_state))
+    return fail(QAOA_ERR_INVALID_ARG, "probabilities: bad n, state type or pointer");
+  if (d_probs && ((uintptr_t)d_probs & 15u)) return fail(QAOA_ERR_INVALID_ARG, "probabilities: misaligned d_probs");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const double es = st == QAOA_C128 ? 16.0 : 8.0;
+  LAUNCH("probabilities", (es + (d_probs ? es / 2.0 : es)) * (double)(1ull << n), s,
+         launch_probs(n, d_state, st == QAOA_C128, d_probs, s, num_sms()));
+  return QAOA_OK;
+}
+
 qaoa_status qaoa_expectation(int n, const void *d_state, qaoa_state_type st, const void *d_costs,
                              qaoa_cost_type ct, void *d_work, size_t work_bytes, double *d_out,
                              qaoa_stream_t stream) {

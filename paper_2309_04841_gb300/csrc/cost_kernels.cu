@@ -316,6 +316,36 @@ cudaError_t launch_cost_stats(int n, const void *cost, int kind, double *partial
   return cudaGetLastError();
 }
 
+// Probabilities |psi_x|^2: into a real array (float for complex64, double for
+// complex128), or in place (psi_x <- |psi_x|^2 + 0i).  One amplitude per
+// thread-iteration; each thread reads its own amplitude before writing it.
+template <typename C2, typename R>
+__global__ void __launch_bounds__(256) k_probs(uint64_t N, C2 *psi, R *out) {
+  for (uint64_t x = blockIdx.x * 256ull + threadIdx.x; x < N; x += (uint64_t)gridDim.x * 256ull) {
+    const C2 a = psi[x];
+    const R pr = a.x * a.x + a.y * a.y;
+    if (out) {
+      out[x] = pr;
+    } else {
+      C2 z;
+      z.x = pr;
+      z.y = 0;
+      psi[x] = z;
+    }
+  }
+}
+
+cudaError_t launch_probs(int n, void *psi, bool c128, void *out, cudaStream_t s, int nsm) {
+  const uint64_t N = 1ull << n;
+  if (c128)
+    k_probs<double2, double><<<grid_for(n, nsm, 8), 256, 0, s>>>(
+        N, reinterpret_cast<double2 *>(psi), reinterpret_cast<double *>(out));
+  else
+    k_probs<float2, float><<<grid_for(n, nsm, 8), 256, 0, s>>>(
+        N, reinterpret_cast<float2 *>(psi), reinterpret_cast<float *>(out));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_expect(int n, const void *psi, bool c128, const void *cost, int kind,
                           double fmin, double *partials, unsigned *counter, double *out, int which,
                           cudaStream_t s, int nsm) {

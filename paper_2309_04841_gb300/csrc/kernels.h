@@ -37,6 +37,7 @@ struct EdgeChunk {
 cudaError_t launch_terms(const TermChunk &P, cudaStream_t s, int nsm);
 cudaError_t launch_labs(int n, int32_t *out, cudaStream_t s, int nsm);
 cudaError_t launch_labs_u16(int n, uint16_t *out, cudaStream_t s, int nsm);
+cudaError_t launch_probs(int n, void *psi, bool c128, void *out, cudaStream_t s, int nsm);
 cudaError_t launch_convert(int n, const void *src, int src_kind, void *dst, int dst_kind,
                            cudaStream_t s, int nsm);
 cudaError_t launch_maxcut(const EdgeChunk &P, cudaStream_t s, int nsm);

@@ -95,6 +95,7 @@ def lib():
             "qaoa_cost_stats_compute": ([I, P, I, P, Z, P, P], I),
             "qaoa_simulate": ([I, P, I, P, P, P, I, P, I, I, P, Z, P, P], I),
             "qaoa_expectation": ([I, P, I, P, I, P, Z, P, P], I),
+            "qaoa_probabilities": ([I, P, I, P, P], I),
             "qaoa_overlap": ([I, P, I, P, I, P, P, Z, P, P], I),
             "qaoa_grad": ([I, P, I, P, P, P, I, P, P, I, P, Z, P, P], I),
             "qaoa_workspace_check": ([P, Z, P], I),
@@ -331,6 +332,57 @@ def simulate_noalloc(costs, stats, gammas, betas, state=None, state_type=C64, in
                                        state_type_of(state), 1 if init_plus else 0, _ptr(out),
                                        _stream()))
     return state, out
+
+
+def probabilities(state, preserve_state=True, out=None):
+    """|psi_x|^2 (Sec. 4 get_probabilities).  preserve_state=True writes a
+    new real tensor (float32 for complex64, float64 for complex128); False
+    squares in place and returns the real view of `state` (each amplitude
+    becomes |psi_x|^2 + 0i)."""
+    torch = _torch()
+    n = _n_of(state)
+    if preserve_state:
+        if out is None:
+            rd = torch.float32 if state.dtype == torch.complex64 else torch.float64
+            out = torch.empty(1 << n, dtype=rd, device=state.device)
+        _check(lib().qaoa_probabilities(n, _ptr(state), state_type_of(state), _ptr(out), _stream()))
+        return out
+    _check(lib().qaoa_probabilities(n, _ptr(state), state_type_of(state), None, _stream()))
+    return state.real
+
+
+def optimize(costs, stats, gammas, betas, steps=100, lr=0.02, betas_adam=(0.9, 0.999),
+             eps=1e-8, state_type=C64):
+    """The optimizer loop of Fig. 1: Adam on the QAOA objective with the
+    gradient of every step from qaoa_grad (forward + adjoint sweep on the
+    device); the loop itself runs on the host.  Returns (gammas, betas,
+    history) with history[k] = E at the angles of step k; the last entry is
+    the energy at the returned angles."""
+    import numpy as np
+    torch = _torch()
+    x = np.concatenate([np.asarray(gammas, np.float64), np.asarray(betas, np.float64)])
+    p = len(gammas)
+    m = np.zeros_like(x)
+    v = np.zeros_like(x)
+    n = _n_of(costs)
+    state = torch.empty(1 << n, dtype=state_dtype(state_type), device="cuda")
+    lam = torch.empty_like(state)
+    work = workspace(n)
+    out = torch.empty(2 + 2 * p, dtype=torch.float64, device="cuda")
+    hist = []
+    b1, b2 = betas_adam
+    for t in range(1, steps + 1):
+        grad(costs, stats, x[:p], x[p:], state=state, lam=lam, state_type=state_type, work=work,
+             out=out)
+        r = out.cpu().numpy()
+        hist.append(float(r[0]))
+        gr = r[2:]
+        m = b1 * m + (1 - b1) * gr
+        v = b2 * v + (1 - b2) * gr * gr
+        x = x - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+    _, o = simulate(costs, stats, x[:p], x[p:], state=state, state_type=state_type, work=work)
+    hist.append(float(o[0]))
+    return x[:p].copy(), x[p:].copy(), hist
 
 
 def expectation(state, costs, work=None, out=None):

@@ -162,3 +162,11 @@ def test_u16_validation_without_gpu(L):
     ok = Q.CostStats(0.0, 5.0, 1)
     assert L.qaoa_convert_costs(4, P(256), Q.COST_F32, C.byref(ok), P(512), Q.COST_U16, None) == 1
     assert L.qaoa_convert_costs(4, P(256), Q.COST_I32, None, P(512), Q.COST_U16, None) == 1
+
+
+def test_probabilities_validation_without_gpu(L):
+    P = C.c_void_p
+    assert L.qaoa_probabilities(0, P(256), Q.C64, P(512), None) == 1
+    assert L.qaoa_probabilities(10, P(264), Q.C64, P(512), None) == 1  # misaligned state
+    assert L.qaoa_probabilities(10, P(256), Q.C64, P(520), None) == 1  # misaligned output
+    assert L.qaoa_probabilities(10, P(256), 7, None, None) == 1        # bad state type
