@@ -16,6 +16,8 @@
  *   - uniform SU(2) transform (the mixer) ... Algorithm 2, Sec. 3.2
  *   - QAOA simulation ....................... Algorithm 3
  *   - expectation / ground-state overlap .... Sec. 3.1 (inner product), Sec. 4
+ *   - XY mixers (ring, complete graph) ...... Sec. 3.2 (SU(4) extension of
+ *     Algorithms 1-2), as the ordered product of the edge gates
  *   - adjoint gradient ...................... not in the paper; textbook
  *     reverse-mode differentiation of Algorithm 3 that keeps every
  *     intermediate state.
@@ -211,6 +213,73 @@ void oracle_simulate(int n, const double *f, int p, const double *gammas,
         oracle_apply_phase(n, psi, f, gammas[l]);
         oracle_apply_mixer(n, psi, betas[l]);
     }
+}
+
+/* ------------------------------------------------------------ XY mixers */
+
+/*
+ * exp(-i beta (X_i X_j + Y_i Y_j) / 2) on qubits i != j, in place (Sec. 3.2,
+ * the SU(4) extension of Algorithm 1).  (XX + YY) / 2 swaps the two basis
+ * states whose bits i, j are 01 and 10 and annihilates 00 and 11, so the gate
+ * is the identity on the latter and [[cos b, -i sin b], [-i sin b, cos b]] on
+ * each pair of states that differ exactly in bits i and j.
+ */
+void oracle_apply_xy(int n, cplx *psi, int i, int j, double beta)
+{
+    uint64_t N = (uint64_t)1 << n, mi = (uint64_t)1 << i, mj = (uint64_t)1 << j;
+    cplx c = cos(beta), s = -I * sin(beta);
+    for (uint64_t x = 0; x < N; ++x) {
+        if ((x & mi) && !(x & mj)) {
+            uint64_t y = x ^ mi ^ mj;
+            cplx a = psi[x], b = psi[y];
+            psi[x] = c * a + s * b;
+            psi[y] = s * a + c * b;
+        }
+    }
+}
+
+/*
+ * XY mixer of a graph on the n qubits: the product of the edge gates, the
+ * first edge applied first.  graph 1 = ring: (0,1), (1,2), ..., (n-2,n-1),
+ * then (n-1,0) when n >= 3; graph 2 = complete: (i,j), i < j, in
+ * lexicographic order.  (The paper names the graphs, not the order.)
+ */
+void oracle_apply_xy_mixer(int n, cplx *psi, int graph, double beta)
+{
+    if (graph == 1) {
+        for (int q = 0; q + 1 < n; ++q)
+            oracle_apply_xy(n, psi, q, q + 1, beta);
+        if (n >= 3)
+            oracle_apply_xy(n, psi, n - 1, 0, beta);
+    } else {
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j)
+                oracle_apply_xy(n, psi, i, j, beta);
+    }
+}
+
+/* Algorithm 3 with the XY mixer, from the state in psi (no |+> start: the XY
+ * mixer keeps the Hamming weight, so the caller picks the sector). */
+void oracle_simulate_xy(int n, const double *f, int p, const double *gammas,
+                        const double *betas, cplx *psi, int graph)
+{
+    for (int l = 0; l < p; ++l) {
+        oracle_apply_phase(n, psi, f, gammas[l]);
+        oracle_apply_xy_mixer(n, psi, graph, betas[l]);
+    }
+}
+
+/* Dicke state |D^n_k>: the uniform superposition of the C(n, k) basis
+ * states of Hamming weight k. */
+void oracle_dicke(int n, int k, cplx *psi)
+{
+    uint64_t N = (uint64_t)1 << n, cnt = 0;
+    for (uint64_t x = 0; x < N; ++x)
+        if (__builtin_popcountll(x) == k)
+            ++cnt;
+    double a = cnt ? 1.0 / sqrt((double)cnt) : 0.0;
+    for (uint64_t x = 0; x < N; ++x)
+        psi[x] = __builtin_popcountll(x) == k ? a : 0.0;
 }
 
 /* Pairwise (recursive halving) sum of v[0..len). */

@@ -38,6 +38,10 @@ def lib():
         L.oracle_overlap.argtypes = [C.c_int, P, P]
         L.oracle_overlap.restype = C.c_double
         L.oracle_grad.argtypes = [C.c_int, P, C.c_int, P, P, P, P, P]
+        L.oracle_apply_xy.argtypes = [C.c_int, P, C.c_int, C.c_int, C.c_double]
+        L.oracle_apply_xy_mixer.argtypes = [C.c_int, P, C.c_int, C.c_double]
+        L.oracle_simulate_xy.argtypes = [C.c_int, P, C.c_int, P, P, P, C.c_int]
+        L.oracle_dicke.argtypes = [C.c_int, C.c_int, P]
         L.oracle_grad.restype = C.c_int
         _lib = L
     return _lib
@@ -138,6 +142,38 @@ def simulate(n, f, gammas, betas, psi0=None):
         psi = np.ascontiguousarray(psi0, dtype=np.complex128).copy()
         init = 0
     lib().oracle_simulate(n, _p(f), len(g), _p(g), _p(b), _p(psi), init)
+    return psi
+
+
+XY_RING, XY_COMPLETE = 1, 2
+
+
+def apply_xy(n, psi, i, j, beta):
+    psi = np.ascontiguousarray(psi, dtype=np.complex128).copy()
+    lib().oracle_apply_xy(n, _p(psi), int(i), int(j), float(beta))
+    return psi
+
+
+def apply_xy_mixer(n, psi, graph, beta):
+    psi = np.ascontiguousarray(psi, dtype=np.complex128).copy()
+    lib().oracle_apply_xy_mixer(n, _p(psi), int(graph), float(beta))
+    return psi
+
+
+def simulate_xy(n, f, gammas, betas, psi0, graph):
+    """Algorithm 3 with the XY mixer of `graph` from psi0; complex128."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(gammas, dtype=np.float64)
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    assert len(g) == len(b)
+    psi = np.ascontiguousarray(psi0, dtype=np.complex128).copy()
+    lib().oracle_simulate_xy(n, _p(f), len(g), _p(g), _p(b), _p(psi), int(graph))
+    return psi
+
+
+def dicke(n, k):
+    psi = np.empty(1 << n, dtype=np.complex128)
+    lib().oracle_dicke(n, k, _p(psi))
     return psi
 
 

@@ -396,3 +396,117 @@ def test_labs_costs_congruent_mod_4(orc, n):
     f = orc.labs_costs(n).astype(np.int64)
     odd = sum(1 for k in range(1, n) if (n - k) % 2)
     assert np.all(f % 4 == odd % 4)
+
+
+# ------------------------------------------------------------- XY mixers
+
+PX = np.array([[0, 1], [1, 0]], dtype=complex)
+PY = np.array([[0, -1j], [1j, 0]], dtype=complex)
+
+
+def dense_pauli_pair(n, i, j, P):
+    """P_i P_j as a dense 2^n matrix (qubit q = bit q, kron puts bit n-1 first)."""
+    op = np.array([[1.0 + 0j]])
+    for q in range(n - 1, -1, -1):
+        op = np.kron(op, P if q in (i, j) else np.eye(2))
+    return op
+
+
+def dense_xy_term(n, i, j):
+    return 0.5 * (dense_pauli_pair(n, i, j, PX) + dense_pauli_pair(n, i, j, PY))
+
+
+def xy_edges(n, graph):
+    if graph == 1:
+        e = [(q, q + 1) for q in range(n - 1)]
+        return e + [(n - 1, 0)] if n >= 3 else e
+    return [(i, j) for i in range(n) for j in range(i + 1, n)]
+
+
+def rand_state(n, seed):
+    v = I.random_state(n, seed)
+    return v / np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("n,i,j", [(2, 0, 1), (3, 0, 2), (4, 3, 1), (4, 1, 2)])
+def test_xy_gate_matches_dense_expm(orc, n, i, j):
+    # the SU(4) gate is exp(-i beta (X_i X_j + Y_i Y_j) / 2), by brute force
+    psi = rand_state(n, 7 + i + j)
+    for beta in (0.37, -1.3, 2.9):
+        want = sl.expm(-1j * beta * dense_xy_term(n, i, j)) @ psi
+        np.testing.assert_allclose(orc.apply_xy(n, psi, i, j, beta), want, atol=1e-13)
+
+
+@pytest.mark.parametrize("graph", [1, 2])
+@pytest.mark.parametrize("n", [3, 4, 5])
+def test_xy_mixer_is_the_ordered_product(orc, n, graph):
+    # the mixer is the product of the edge gates, first edge applied first,
+    # built here from dense matrix exponentials in the stated order
+    beta = 0.61
+    U = np.eye(1 << n, dtype=complex)
+    for i, j in xy_edges(n, graph):
+        U = sl.expm(-1j * beta * dense_xy_term(n, i, j)) @ U
+    psi = rand_state(n, 30 + n)
+    np.testing.assert_allclose(orc.apply_xy_mixer(n, psi, graph, beta), U @ psi, atol=1e-12)
+
+
+def test_xy_single_edge_is_exact_exponential(orc):
+    # n = 2: one edge, so the mixer is exp(-i beta M) exactly; on |01> it is
+    # cos(b)|01> - i sin(b)|10>, and |00>, |11> are untouched
+    beta = 0.83
+    for graph in (1, 2):
+        e01 = np.zeros(4, complex)
+        e01[1] = 1.0
+        out = orc.apply_xy_mixer(2, e01, graph, beta)
+        np.testing.assert_allclose(out, [0, np.cos(beta), -1j * np.sin(beta), 0], atol=1e-15)
+        for k in (0, 3):
+            e = np.zeros(4, complex)
+            e[k] = 1.0
+            np.testing.assert_allclose(orc.apply_xy_mixer(2, e, graph, beta), e, atol=1e-15)
+
+
+@pytest.mark.parametrize("graph", [1, 2])
+def test_xy_preserves_hamming_weight_distribution(orc, graph):
+    n = 7
+    f = orc.labs_costs(n).astype(float)
+    psi = rand_state(n, 41)
+    w = np.array([bin(x).count("1") for x in range(1 << n)])
+    out = orc.simulate_xy(n, f, [0.2, 0.05], [0.7, 1.9], psi, graph)
+    for k in range(n + 1):
+        assert abs(np.sum(np.abs(out[w == k]) ** 2) - np.sum(np.abs(psi[w == k]) ** 2)) < 1e-12
+
+
+@pytest.mark.parametrize("graph", [1, 2])
+def test_xy_product_is_second_order_close_to_exp_of_sum(orc, graph):
+    # the ordered product agrees with exp(-i beta sum_edges term) up to
+    # O(beta^2): halving beta divides the difference by about 4
+    n = 5
+    M = sum(dense_xy_term(n, i, j) for i, j in xy_edges(n, graph))
+    psi = rand_state(n, 52)
+    errs = []
+    for beta in (2e-2, 1e-2):
+        exact = sl.expm(-1j * beta * M) @ psi
+        errs.append(np.linalg.norm(orc.apply_xy_mixer(n, psi, graph, beta) - exact))
+    assert 3.5 < errs[0] / errs[1] < 4.5
+    assert errs[1] < 1e-3
+
+
+@pytest.mark.parametrize("n,k", [(1, 0), (4, 2), (6, 3), (7, 0), (7, 7)])
+def test_dicke_state(orc, n, k):
+    from math import comb
+    psi = orc.dicke(n, k)
+    w = np.array([bin(x).count("1") for x in range(1 << n)])
+    assert np.all(psi[w != k] == 0)
+    np.testing.assert_allclose(psi[w == k], 1 / np.sqrt(comb(n, k)), rtol=1e-15)
+
+
+def test_simulate_xy_is_phase_then_mixer(orc):
+    n = 5
+    f = orc.labs_costs(n).astype(float)
+    psi0 = orc.dicke(n, 2)
+    g, b = [0.3, 0.11], [0.9, 0.4]
+    want = psi0
+    for gl, bl in zip(g, b):
+        want = np.exp(-1j * gl * f) * want
+        want = orc.apply_xy_mixer(n, want, 1, bl)
+    np.testing.assert_allclose(orc.simulate_xy(n, f, g, b, psi0, 1), want, atol=1e-14)
