@@ -191,6 +191,40 @@ qaoa_status qaoa_cost_stats_compute(int n, const void *d_costs,
                                     size_t work_bytes, qaoa_cost_stats *h_out,
                                     qaoa_stream_t stream);
 
+/* ------------------------------------------------------------- XY mixers */
+
+/*
+ * Hamming-weight-preserving XY mixer M = sum_{<i,j>} (X_i X_j + Y_i Y_j) / 2
+ * over the edges of a ring or a complete graph on the qubits (Sec. 3.2, the
+ * SU(4) extension of Algorithms 1-2).  exp(-i beta M) is taken as the
+ * product of the edge gates exp(-i beta (X_i X_j + Y_i Y_j) / 2), first edge
+ * first: ring (0,1), (1,2), ..., (n-2,n-1), (n-1,0) (the last one for n >= 3);
+ * complete (i,j), i < j, in lexicographic order.
+ */
+typedef enum { QAOA_XY_RING = 1, QAOA_XY_COMPLETE = 2 } qaoa_xy_graph;
+
+/*
+ * Algorithm 3 with the XY mixer of `graph`: p layers of phase then mixer on
+ * the state in d_state (the start state is the caller's, e.g. a Dicke state
+ * from qaoa_dicke_state, since the mixer keeps the Hamming weight).  Other
+ * arguments as qaoa_simulate (init_plus does not exist here; stats is needed
+ * only with d_out, which receives [E, O] of the final state).  n >= 2.
+ * Asynchronous.
+ */
+qaoa_status qaoa_simulate_xy(int n, const void *d_costs, qaoa_cost_type ct,
+                             const qaoa_cost_stats *stats, const double *gammas,
+                             const double *betas, int p, int graph, void *d_state,
+                             qaoa_state_type st, void *d_work, size_t work_bytes,
+                             double *d_out, qaoa_stream_t stream);
+
+/*
+ * Dicke state |D^n_k>: amplitude C(n,k)^{-1/2} on every basis state of
+ * Hamming weight k, 0 elsewhere.  d_state: device, 2^n amplitudes of type st,
+ * 16-byte aligned.  0 <= k <= n.  Asynchronous.
+ */
+qaoa_status qaoa_dicke_state(int n, int k, void *d_state, qaoa_state_type st,
+                             qaoa_stream_t stream);
+
 /* ------------------------------------------------------------- workspace */
 
 /*

@@ -21,7 +21,8 @@ UNITS = [("api.cu", "api.o", []), ("pass_kernels.cu", "pass_kernels.o", []),
          ("small_kernels.cu", "small_kernels.o", []), ("cost_kernels.cu", "cost_kernels.o", []),
          ("profile.cu", "profile.o", []), ("tma_kernels.cu", "tma_kernels.o", []),
          ("tma_kernels.cu", "tma_kernels_u16.o", ["-DQAOA_TMA_CW=2"]),
-         ("noalloc.cu", "noalloc.o", []), ("serve.cu", "serve.o", [])]
+         ("noalloc.cu", "noalloc.o", []), ("serve.cu", "serve.o", []),
+         ("xy_kernels.cu", "xy_kernels.o", [])]
 SOURCES = sorted({u[0] for u in UNITS})
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1098,6 +1098,159 @@ qaoa_status qaoa_simulate(int n, const void *d_costs, qaoa_cost_type ct, const q
              : tiled_forward<double>(n, d_costs, ct, stats, gammas, betas, p, d_state, init_plus, ws, d_out, s);
 }
 
+// ------------------------------------------------------------- XY mixers
+
+struct XyOp {
+  bool tile;      // a tile pass, else one gate over the whole state
+  int tb, c, h;   // tile geometry
+  std::vector<std::pair<int, int>> gates;  // qubit pairs, in order
+};
+
+std::vector<std::pair<int, int>> xy_edges(int n, int graph) {
+  std::vector<std::pair<int, int>> e;
+  if (graph == QAOA_XY_RING) {
+    for (int q = 0; q + 1 < n; ++q) e.push_back({q, q + 1});
+    if (n >= 3) e.push_back({n - 1, 0});
+  } else {
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) e.push_back({i, j});
+  }
+  return e;
+}
+
+// Packs the ordered edge list into passes: consecutive gates share a tile
+// while both qubits of each lie in it (passengers 0..c-1 or rows h..h+W-1).
+std::vector<XyOp> xy_schedule(int n, const std::vector<std::pair<int, int>> &edges) {
+  const int TB = n < kXyMaxTb ? n : kXyMaxTb;
+  const int c = n <= kXyMaxTb ? n : 4, W = TB - c;
+  std::vector<XyOp> ops;
+  auto fits = [&](const XyOp &o, int q) { return q < o.c || (q >= o.h && q < o.h + o.tb - o.c); };
+  for (const auto &e : edges) {
+    if (!ops.empty() && ops.back().tile && (int)ops.back().gates.size() < kXyMaxGates &&
+        fits(ops.back(), e.first) && fits(ops.back(), e.second)) {
+      ops.back().gates.push_back(e);
+      continue;
+    }
+    XyOp o;
+    o.tile = true;
+    o.tb = TB;
+    if (e.first < TB && e.second < TB) {  // the contiguous low tile
+      o.c = TB;
+      o.h = TB;
+    } else {
+      int a = e.first, b = e.second;
+      if (a > b) std::swap(a, b);
+      const int lo = a < c ? b : a;  // lowest qubit that must sit in a row
+      if (a >= c && b - a >= W) {
+        o.tile = false;  // no tile holds both: one gate over the state
+      } else {
+        o.c = c;
+        o.h = lo < n - W ? lo : n - W;
+      }
+    }
+    o.gates.push_back(e);
+    ops.push_back(o);
+  }
+  return ops;
+}
+
+qaoa_status qaoa_simulate_xy(int n, const void *d_costs, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                             const double *gammas, const double *betas, int p, int graph, void *d_state,
+                             qaoa_state_type st, void *d_work, size_t work_bytes, double *d_out,
+                             qaoa_stream_t stream) {
+  if (n < 2) return fail(QAOA_ERR_INVALID_ARG, "simulate_xy: n must be >= 2");
+  qaoa_status r = check_common(n, d_costs, ct, d_state, st);
+  if (r != QAOA_OK) return r;
+  if (graph != QAOA_XY_RING && graph != QAOA_XY_COMPLETE) return fail(QAOA_ERR_INVALID_ARG, "simulate_xy: bad graph");
+  r = check_angles(gammas, betas, p);
+  if (r != QAOA_OK) return r;
+  if (d_out && (((uintptr_t)d_out & 7u) || !stats)) return fail(QAOA_ERR_INVALID_ARG, "simulate_xy: d_out needs stats and 8-byte alignment");
+  Ws ws;
+  r = get_ws(n, d_work, work_bytes, ws);
+  if (r != QAOA_OK) return r;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool c128 = st == QAOA_C128;
+  const int nsm = num_sms();
+  const double N = (double)(1ull << n), es = c128 ? 16.0 : 8.0;
+  std::vector<XyOp> ops = xy_schedule(n, xy_edges(n, graph));
+  if (ops.empty() || !ops.front().tile) {  // the phase rides on a tile pass
+    XyOp o;
+    o.tile = true;
+    o.tb = n < kXyMaxTb ? n : kXyMaxTb;
+    o.c = o.tb;
+    o.h = o.tb;
+    ops.insert(ops.begin(), o);
+  }
+  static XyPass P;
+  static std::mutex *mu = new std::mutex();
+  std::lock_guard<std::mutex> lock(*mu);
+  for (int l = 0; l < p; ++l) {
+    // the pair rotation by beta as three shears: beta reduced to [-pi/2, pi/2]
+    // (a rotation by pi is the exact factor -1)
+    double br = std::remainder(betas[l], kTwoPi);  // (-pi, pi]
+    int neg = 0;
+    if (br > kTwoPi / 4) {
+      br -= kTwoPi / 2;
+      neg = 1;
+    } else if (br < -kTwoPi / 4) {
+      br += kTwoPi / 2;
+      neg = 1;
+    }
+    const double tb2 = std::tan(br / 2), sb = std::sin(br);
+    const double g2 = gammas[l] / kTwoPi;
+    for (size_t k = 0; k < ops.size(); ++k) {
+      const XyOp &o = ops[k];
+      if (!o.tile) {
+        LAUNCH("xy_gate", es * N, s,
+               launch_xy_gate(d_state, c128, n, o.gates[0].first, o.gates[0].second, tb2, sb, neg, s,
+                              nsm));
+        continue;
+      }
+      memset(&P, 0, sizeof(P));
+      P.psi = d_state;
+      P.cost = d_costs;
+      P.cost_kind = cost_kind(ct);
+      P.tb = o.tb;
+      P.c = o.c;
+      P.h = o.h;
+      P.ntiles = 1ull << (n - o.tb);
+      P.has_phase = k == 0;
+      P.g2pi = g2;
+      P.g_hi = (float)g2;
+      P.g_lo = (float)(g2 - (double)P.g_hi);
+      P.tb2 = tb2;
+      P.sb = sb;
+      P.neg = neg;
+      P.ngates = (int)o.gates.size();
+      auto tbit = [&](int q) { return q < o.c ? q : o.c + (q - o.h); };
+      for (int g = 0; g < P.ngates; ++g) {
+        P.ga[g] = (uint8_t)tbit(o.gates[g].first);
+        P.gb[g] = (uint8_t)tbit(o.gates[g].second);
+      }
+      LAUNCH("xy_tile", 2.0 * es * N + (P.has_phase ? cost_bytes(ct) * N : 0.0), s,
+             launch_xy_tile(P, c128, s, nsm));
+    }
+  }
+  if (d_out) {
+    CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
+    LAUNCH("expect", (es + cost_bytes(ct)) * N, s,
+           launch_expect(n, d_state, c128, d_costs, cost_kind(ct), stats->f_min, ws.partials,
+                         ws.counter, d_out, 2, s, nsm));
+  }
+  return QAOA_OK;
+}
+
+qaoa_status qaoa_dicke_state(int n, int k, void *d_state, qaoa_state_type st, qaoa_stream_t stream) {
+  if (n < 1 || n > QAOA_MAX_N || k < 0 || k > n || !valid_state_type(st) || !aligned16(d_state))
+    return fail(QAOA_ERR_INVALID_ARG, "dicke_state: bad n, k, state type or pointer");
+  double cnk = 1.0;  // C(n, k), exact in float64 for n <= 34
+  for (int i = 1; i <= k; ++i) cnk = cnk * (n - k + i) / i;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  LAUNCH("dicke", (st == QAOA_C128 ? 16.0 : 8.0) * (double)(1ull << n), s,
+         launch_dicke(d_state, st == QAOA_C128, n, k, 1.0 / std::sqrt(cnk), s, num_sms()));
+  return QAOA_OK;
+}
+
 qaoa_status qaoa_probabilities(int n, void *d_state, qaoa_state_type st, void *d_probs,
                                qaoa_stream_t stream) {
   if (n < 1 || n > QAOA_MAX_N || !valid_state_type(st) || !aligned16(d_state))

@@ -253,7 +253,12 @@ __global__ void __launch_bounds__(256) k_expect(int n, const C2 *psi, const void
       te += __ldcg(partials + b * 2);
       to += __ldcg(partials + b * 2 + 1);
     }
-    out[0] = which == 0 ? te : to;
+    if (which == 2) {
+      out[0] = te;
+      out[1] = to;
+    } else {
+      out[0] = which == 0 ? te : to;
+    }
     *counter = 0u;
   }
 }

@@ -155,6 +155,29 @@ cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int
 cudaError_t launch_fwd_tma_u16(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm);
 cudaError_t launch_bwd_tma_u16(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm);
 
+// One XY-mixer pass over tiles of 2^tb amplitudes: qubits 0..c-1 (contiguous)
+// and h..h+tb-c-1; the gates act on tile bits (ga[g], gb[g]) in order.
+constexpr int kXyMaxTb = 12;
+constexpr int kXyMaxGates = 64;
+struct XyPass {
+  void *psi;
+  const void *cost;
+  uint64_t ntiles;
+  int tb, c, h;
+  int cost_kind, has_phase;  // phase exp(-i g f) applied while loading
+  float g_hi, g_lo;          // complex64: g / 2pi = g_hi + g_lo
+  double g2pi;               // complex128: g / 2pi
+  double tb2, sb;            // tan(b/2), sin(b) of the layer's beta reduced to |b| <= pi/2
+  int neg;                   // the reduction took out a factor -1
+  int ngates;
+  uint8_t ga[kXyMaxGates], gb[kXyMaxGates];
+};
+
+cudaError_t launch_xy_tile(const XyPass &P, bool c128, cudaStream_t s, int nsm);
+cudaError_t launch_xy_gate(void *psi, bool c128, int n, int i, int j, double tb2, double sb, int neg,
+                           cudaStream_t s, int nsm);
+cudaError_t launch_dicke(void *psi, bool c128, int n, int k, double amp, cudaStream_t s, int nsm);
+
 cudaError_t launch_small_batch(const SmallJob<float> *d_jobs, int count, int max_n, cudaStream_t s);
 cudaError_t launch_small_batch(const SmallJob<double> *d_jobs, int count, int max_n, cudaStream_t s);
 cudaError_t launch_small(const SmallParams<float> &P, cudaStream_t s);

@@ -96,6 +96,8 @@ def lib():
             "qaoa_simulate": ([I, P, I, P, P, P, I, P, I, I, P, Z, P, P], I),
             "qaoa_expectation": ([I, P, I, P, I, P, Z, P, P], I),
             "qaoa_probabilities": ([I, P, I, P, P], I),
+            "qaoa_simulate_xy": ([I, P, I, P, P, P, I, I, P, I, P, Z, P, P], I),
+            "qaoa_dicke_state": ([I, I, P, I, P], I),
             "qaoa_overlap": ([I, P, I, P, I, P, P, Z, P, P], I),
             "qaoa_grad": ([I, P, I, P, P, P, I, P, P, I, P, Z, P, P], I),
             "qaoa_workspace_check": ([P, Z, P], I),
@@ -332,6 +334,36 @@ def simulate_noalloc(costs, stats, gammas, betas, state=None, state_type=C64, in
                                        state_type_of(state), 1 if init_plus else 0, _ptr(out),
                                        _stream()))
     return state, out
+
+
+XY_RING, XY_COMPLETE = 1, 2
+
+
+def dicke_state(n, k, state_type=C64, out=None):
+    """|D^n_k> on the device."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(1 << n, dtype=state_dtype(state_type), device="cuda")
+    _check(lib().qaoa_dicke_state(n, k, _ptr(out), state_type_of(out), _stream()))
+    return out
+
+
+def simulate_xy(costs, stats, gammas, betas, state, graph=XY_RING, work=None, out=None,
+                reduce=True):
+    """Algorithm 3 with the XY mixer (ring or complete graph) on `state`
+    (updated in place).  Returns (state, out), out = [E, O] when reduce."""
+    torch = _torch()
+    n = _n_of(costs)
+    g, b = _angles(gammas, betas)
+    if work is None:
+        work = workspace(n)
+    if reduce and out is None:
+        out = torch.empty(2, dtype=torch.float64, device="cuda")
+    _check(lib().qaoa_simulate_xy(n, _ptr(costs), cost_type_of(costs), C.byref(stats), _np_ptr(g),
+                                  _np_ptr(b), len(g), graph, _ptr(state), state_type_of(state),
+                                  _ptr(work), work.numel(), _ptr(out) if reduce else None,
+                                  _stream()))
+    return state, (out if reduce else None)
 
 
 def probabilities(state, preserve_state=True, out=None):

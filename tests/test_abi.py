@@ -170,3 +170,19 @@ def test_probabilities_validation_without_gpu(L):
     assert L.qaoa_probabilities(10, P(264), Q.C64, P(512), None) == 1  # misaligned state
     assert L.qaoa_probabilities(10, P(256), Q.C64, P(520), None) == 1  # misaligned output
     assert L.qaoa_probabilities(10, P(256), 7, None, None) == 1        # bad state type
+
+
+def test_xy_validation_without_gpu(L):
+    P = C.c_void_p
+    stats = Q.CostStats(0.0, 1.0, 1)
+    g = np.zeros(2)
+    # bad graph, n < 2, NULL stats with d_out
+    assert L.qaoa_simulate_xy(10, P(256), 0, C.byref(stats), Q._np_ptr(g), Q._np_ptr(g), 2, 3,
+                              P(512), 0, P(1024), 1 << 30, None, None) == 1
+    assert L.qaoa_simulate_xy(1, P(256), 0, C.byref(stats), Q._np_ptr(g), Q._np_ptr(g), 2, 1,
+                              P(512), 0, P(1024), 1 << 30, None, None) == 1
+    assert L.qaoa_simulate_xy(10, P(256), 0, None, Q._np_ptr(g), Q._np_ptr(g), 2, 1,
+                              P(512), 0, P(1024), 1 << 30, P(2048), None) == 1
+    assert L.qaoa_dicke_state(10, 11, P(256), 0, None) == 1
+    assert L.qaoa_dicke_state(10, -1, P(256), 0, None) == 1
+    assert L.qaoa_dicke_state(10, 3, P(260), 0, None) == 1
