@@ -934,8 +934,15 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
   const CUtensorMapSwizzle sw = swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                                 : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                                       : CU_TENSOR_MAP_SWIZZLE_NONE;
-  const CUresult r = fn(map, dt, 5, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  // L2 promotion no wider than a box row (2^c contiguous elements): wider
+  // promotion fetches neighbouring rows that belong to other tiles and are
+  // often evicted before those tiles are loaded
+  const uint64_t row_bytes = (1ull << c) * e;
+  const CUtensorMapL2promotion l2 = row_bytes <= 64    ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
+                                    : row_bytes <= 128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                                                       : CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
+  const CUresult r = fn(map, dt, 5, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, l2,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 #endif  // QAOA_TMA_CW == 4
