@@ -302,6 +302,30 @@ def run_ours(a, ws, rank, local):
     result16 = out.cpu().numpy()
     del costs16
 
+    # ---- the XY ring mixer (Sec. 3.2) on LABS n = 28 from the half-filling
+    # Dicke state: forward simulation with E and O, 4 layers
+    nx, px = 28, 4
+    fx = Q.labs_costs(nx)
+    sx = Q.cost_stats_compute(fx)
+    gx, bx = I.angles(px, 6), I.angles(px, 16)
+    sv = Q.dicke_state(nx, nx // 2)
+    wx = Q.workspace(nx)
+    ox = torch.empty(2, dtype=torch.float64, device="cuda")
+    for _ in range(a.warmup):
+        Q.simulate_xy(fx, sx, gx, bx, sv, Q.XY_RING, work=wx, out=ox)
+    torch.cuda.synchronize()
+    Q.profile_read(reset=True)
+    Q.profile_enable(True)
+    t0.record(stream)
+    for _ in range(a.steps):
+        Q.simulate_xy(fx, sx, gx, bx, sv, Q.XY_RING, work=wx, out=ox)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    Q.profile_enable(False)
+    msx = t0.elapsed_time(t1) / a.steps
+    px_prof = Q.profile_read(reset=True).get("xy_tile", None)
+    del fx, sv
+
     # ---- end to end through the public API with host buffers: angles from
     # pinned host memory (they travel in the launch parameters), the result
     # read back into pinned host memory every step
@@ -358,7 +382,13 @@ def run_ours(a, ws, rank, local):
             "value": a.steps * ws / (ms16 / 1000.0), "unit": UNIT, "ms_per_step": ms16 / a.steps,
             "note": ("same workload and angles, cost vector held as uint16 values "
                      "(qaoa_convert_costs from the int32 vector; lossless since LABS f < 2^16)"),
-            "result_identical": bool(np.array_equal(result16, result))}},
+            "result_identical": bool(np.array_equal(result16, result))},
+            "xy_ring": {
+                "workload": f"XY ring mixer, LABS n={nx}, p={px}, from the Dicke state k={nx // 2}, "
+                            "forward simulation + energy/overlap, complex64",
+                "ms_per_eval": msx, "layers_per_s": px * 1000.0 / msx,
+                "tile_pass_GBps": (px_prof["bytes"] / px_prof["ms"] / 1e6) if px_prof else None,
+                "tile_passes_per_layer": (px_prof["launches"] // (a.steps * px)) if px_prof else None}},
         "precompute_ms": precompute_ms,
         "result": {"energy": float(result[0]), "overlap": float(result[1])},
     }
@@ -411,40 +441,50 @@ def serving_bench(count=400, nmin=16, nmax=26):
         srv.wait(t, r["p"])
     sat_tput = count / (time.perf_counter() - t0)
     srv.close()
-    # open loop: Poisson arrivals at 80% of the saturated throughput
-    rate = 0.8 * sat_tput
-    arr = I.poisson_arrivals(count, rate)
-    srv = Q.Server(arena, max_inflight=8)
-    for r in reqs[:8]:
-        srv.wait(sub(srv, r), r["p"])
-    base = time.perf_counter()
-    ts = []
-    for a, r in zip(arr, reqs):
-        d = base + a - time.perf_counter()
-        if d > 0:
-            time.sleep(d)
-        ts.append(sub(srv, r))
-    lat = []
-    for t, r in zip(ts, reqs):
-        res = srv.wait(t, r["p"])
-        lat.append(res["finish_s"] - res["submit_s"])
-    srv.close()
-    lat = np.sort(np.array(lat)) * 1000
-    # the plain path under the same arrivals: a FIFO single-server queue
-    fin, plat = 0.0, []
-    for a, s in zip(arr, service):
-        fin = max(fin, a) + s
-        plat.append(fin - a)
-    plat = np.sort(np.array(plat)) * 1000
     pct = lambda v, q: float(v[min(len(v) - 1, int(round(q * (len(v) - 1))))])
+
+    def open_loop(load):
+        """Poisson arrivals at `load` x the saturated server throughput: the
+        server's latencies (finish - submit) and those of the plain path as a
+        FIFO single-server queue of the measured service times."""
+        rate = load * sat_tput
+        arr = I.poisson_arrivals(count, rate)
+        srv = Q.Server(arena, max_inflight=8)
+        for r in reqs[:8]:
+            srv.wait(sub(srv, r), r["p"])
+        base = time.perf_counter()
+        ts = []
+        for a, r in zip(arr, reqs):
+            d = base + a - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            ts.append(sub(srv, r))
+        lat = []
+        for t, r in zip(ts, reqs):
+            res = srv.wait(t, r["p"])
+            lat.append(res["finish_s"] - res["submit_s"])
+        srv.close()
+        lat = np.sort(np.array(lat)) * 1000
+        fin, plat = 0.0, []
+        for a, sv in zip(arr, service):
+            fin = max(fin, a) + sv
+            plat.append(fin - a)
+        plat = np.sort(np.array(plat)) * 1000
+        return {"load": load, "arrival_rate_per_s": rate,
+                "server_p50_ms": pct(lat, 0.5), "server_p99_ms": pct(lat, 0.99),
+                "plain_p50_ms": pct(plat, 0.5), "plain_p99_ms": pct(plat, 0.99)}
+
+    sweep = [open_loop(x) for x in (0.5, 0.8, 0.95)]
+    mid = sweep[1]
     return {"requests": count,
             "recipe": (f"objective+gradient requests, n ~ U{{{nmin}..{nmax}}} (MaxCut rounded up to even), "
                        "p ~ U{1..40}, LABS or MaxCut 3-regular 50/50 (4 graphs per n), complex64; "
-                       f"Poisson arrivals at 0.8 x the saturated server throughput"),
-            "server": {"evals_per_s_saturated": sat_tput, "arrival_rate_per_s": rate,
-                       "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99)},
-            "plain_per_request": {"evals_per_s": plain_tput, "p50_ms": pct(plat, 0.5),
-                                  "p99_ms": pct(plat, 0.99)}}
+                       "Poisson arrivals at 0.5 / 0.8 / 0.95 x the saturated server throughput"),
+            "server": {"evals_per_s_saturated": sat_tput, "arrival_rate_per_s": mid["arrival_rate_per_s"],
+                       "p50_ms": mid["server_p50_ms"], "p99_ms": mid["server_p99_ms"]},
+            "plain_per_request": {"evals_per_s": plain_tput, "p50_ms": mid["plain_p50_ms"],
+                                  "p99_ms": mid["plain_p99_ms"]},
+            "load_sweep": sweep}
 
 
 # ------------------------------------------------------- reference arm
