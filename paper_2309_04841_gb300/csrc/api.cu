@@ -1218,6 +1218,8 @@ qaoa_status qaoa_simulate_xy(int n, const void *d_costs, qaoa_cost_type ct, cons
       P.g2pi = g2;
       P.g_hi = (float)g2;
       P.g_lo = (float)(g2 - (double)P.g_hi);
+      if (P.has_phase && !c128) make_phase(P.ph, gammas[l], ct, stats, 1.0);  // tables or computed
+      else P.ph.mode = 1;
       P.tb2 = tb2;
       P.sb = sb;
       P.neg = neg;

@@ -171,6 +171,7 @@ struct XyPass {
   int neg;                   // the reduction took out a factor -1
   int ngates;
   uint8_t ga[kXyMaxGates], gb[kXyMaxGates];
+  PhaseDigits ph;  // complex64 integer costs: digit tables (mode 0), else computed
 };
 
 cudaError_t launch_xy_tile(const XyPass &P, bool c128, cudaStream_t s, int nsm);

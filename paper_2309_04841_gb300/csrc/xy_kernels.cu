@@ -54,7 +54,32 @@ __device__ __forceinline__ void xy_pair(C2 &u, C2 &w, R t, R s, bool neg) {
   w = xmk<C2>(y1.y, -y1.x);  // -i v
 }
 
-// k with zero bits inserted at positions lo < hi.
+// Two neighbouring amplitudes (p 16-byte aligned): one 16-byte access for
+// complex64.
+__device__ __forceinline__ void ld2(const float2 *p, float2 &a, float2 &b) {
+  const float4 q = *reinterpret_cast<const float4 *>(p);
+  a = make_float2(q.x, q.y);
+  b = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void ld2(const double2 *p, double2 &a, double2 &b) {
+  a = p[0];
+  b = p[1];
+}
+__device__ __forceinline__ void st2(float2 *p, float2 a, float2 b) {
+  *reinterpret_cast<float4 *>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st2(double2 *p, double2 a, double2 b) {
+  p[0] = a;
+  p[1] = b;
+}
+
+// k with zero bits inserted at positions lo < hi (32-bit: tile offsets).
+__device__ __forceinline__ uint32_t insert2_32(uint32_t k, int lo, int hi) {
+  k = ((k >> lo) << (lo + 1)) | (k & ((1u << lo) - 1u));
+  return ((k >> hi) << (hi + 1)) | (k & ((1u << hi) - 1u));
+}
+
+// The same for global indices.
 __device__ __forceinline__ uint64_t insert2(uint64_t k, int lo, int hi) {
   k = ((k >> lo) << (lo + 1)) | (k & ((1ull << lo) - 1ull));
   return ((k >> hi) << (hi + 1)) | (k & ((1ull << hi) - 1ull));
@@ -89,6 +114,29 @@ __device__ __forceinline__ double2 xy_phase(const XyPass &P, double2, uint64_t x
   return make_double2(cs, -sn);
 }
 
+// exp(-i g f_x) from the digit tables (copy q of entry e at e * 16 + q; see
+// PhaseDigits), integer costs only.
+__device__ __forceinline__ float2 xy_phase_tab(const XyPass &P, const float2 *tab, float2, uint64_t x) {
+  const int f = P.cost_kind == kCostU16 ? (int)__ldg(reinterpret_cast<const unsigned short *>(P.cost) + x)
+                                        : __ldg(reinterpret_cast<const int *>(P.cost) + x);
+  const uint32_t d = (uint32_t)(f - P.ph.fmin) >> P.ph.shift;
+  const uint32_t q = threadIdx.x & (kPhaseCopies - 1);
+  if (P.ph.nd == 2) {
+    const float2 a = tab[((d & 63u) << 4) | q];
+    const float2 b = tab[((64u + min(d >> 6, (uint32_t)P.ph.last)) << 4) | q];
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  }
+  const float2 a = tab[((d & 31u) << 4) | q];
+  const float2 b = tab[((32u + ((d >> 5) & 31u)) << 4) | q];
+  const float2 c = tab[((64u + min(d >> 10, (uint32_t)P.ph.last)) << 4) | q];
+  const float2 ab = make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return make_float2(ab.x * c.x - ab.y * c.y, ab.x * c.y + ab.y * c.x);
+}
+
+__device__ __forceinline__ double2 xy_phase_tab(const XyPass &P, const float2 *, double2, uint64_t x) {
+  return xy_phase(P, double2(), x);  // complex128 always computes
+}
+
 // Global index of tile offset t in tile T (bits of t below c are qubits
 // 0..c-1, the others qubits h..; T fills the remaining bits in order).
 __device__ __forceinline__ uint64_t xy_index(const XyPass &P, uint64_t T, uint32_t t) {
@@ -105,26 +153,46 @@ __global__ void __launch_bounds__(256) k_xy_tile(const __grid_constant__ XyPass 
   C2 *s = reinterpret_cast<C2 *>(xy_smem);
   C2 *psi = reinterpret_cast<C2 *>(P.psi);
   const uint32_t TE = 1u << P.tb;
+  float2 *tab = reinterpret_cast<float2 *>(xy_smem + (size_t)TE * sizeof(C2));
   const R th = (R)P.tb2, sn = (R)P.sb;
   const bool neg = P.neg != 0;
+  const bool table = P.has_phase && P.ph.mode == 0;
+  if (table) {
+    for (int i = threadIdx.x; i < P.ph.nent * kPhaseCopies; i += blockDim.x) tab[i] = P.ph.d[i >> 4];
+    __syncthreads();
+  }
   for (uint64_t T = blockIdx.x; T < P.ntiles; T += gridDim.x) {
-    for (uint32_t t = threadIdx.x; t < TE; t += blockDim.x) {
-      const uint64_t x = xy_index(P, T, t);
-      C2 v = psi[x];
-      if (P.has_phase) v = xmul(v, xy_phase(P, v, x));
-      s[t] = v;
+    // pairs of neighbouring amplitudes (tile bit 0 is qubit 0, c >= 1): one
+    // 16-byte load per complex64 pair
+    for (uint32_t t = 2 * threadIdx.x; t < TE; t += 2 * blockDim.x) {
+      const uint64_t x = xy_index(P, T, t);  // even
+      C2 v0, v1;
+      ld2(psi + x, v0, v1);
+      if (P.has_phase) {
+        if (table) {
+          v0 = xmul(v0, xy_phase_tab(P, tab, v0, x));
+          v1 = xmul(v1, xy_phase_tab(P, tab, v1, x + 1));
+        } else {
+          v0 = xmul(v0, xy_phase(P, v0, x));
+          v1 = xmul(v1, xy_phase(P, v1, x + 1));
+        }
+      }
+      s[t] = v0;
+      s[t + 1] = v1;
     }
     __syncthreads();
     for (int g = 0; g < P.ngates; ++g) {
       const int a = P.ga[g], b = P.gb[g];
       const int lo = a < b ? a : b, hi = a < b ? b : a;
       for (uint32_t k = threadIdx.x; k < (TE >> 2); k += blockDim.x) {
-        const uint32_t t0 = (uint32_t)insert2(k, lo, hi);
+        const uint32_t t0 = insert2_32(k, lo, hi);
         xy_pair<C2, R>(s[t0 | (1u << a)], s[t0 | (1u << b)], th, sn, neg);
       }
       __syncthreads();
     }
-    for (uint32_t t = threadIdx.x; t < TE; t += blockDim.x) psi[xy_index(P, T, t)] = s[t];
+    for (uint32_t t = 2 * threadIdx.x; t < TE; t += 2 * blockDim.x) {
+      st2(psi + xy_index(P, T, t), s[t], s[t + 1]);
+    }
     __syncthreads();
   }
 }
@@ -158,18 +226,19 @@ unsigned grid_n(uint64_t work, int nsm) {
 }  // namespace
 
 cudaError_t launch_xy_tile(const XyPass &P, bool c128, cudaStream_t s, int nsm) {
-  const size_t smem = ((size_t)1 << P.tb) * (c128 ? 16 : 8);
+  const size_t tabb = (size_t)kPhaseTabEntries * sizeof(float2);
+  const size_t smem = ((size_t)1 << P.tb) * (c128 ? 16 : 8) + (P.has_phase && P.ph.mode == 0 ? tabb : 0);
   static bool init = false;
   if (!init) {
     cudaError_t e = cudaFuncSetAttribute(k_xy_tile<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(((size_t)1 << kXyMaxTb) * 8));
+                                         (int)(((size_t)1 << kXyMaxTb) * 8 + tabb));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_xy_tile<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(((size_t)1 << kXyMaxTb) * 16));
     if (e != cudaSuccess) return e;
     init = true;
   }
-  const uint64_t cap = (uint64_t)nsm * (c128 ? 2 : 4);
+  const uint64_t cap = (uint64_t)nsm * (c128 ? 3 : 4);  // resident CTAs per SM (shared memory)
   const unsigned grid = (unsigned)(P.ntiles < cap ? P.ntiles : cap);
   if (c128)
     k_xy_tile<double2><<<grid, 256, smem, s>>>(P);
