@@ -9,6 +9,7 @@
 //                      the adjoint repeats the same shapes in reverse.
 // Nothing here allocates device memory: scratch lives in the caller's
 // workspace, per-layer constants travel in the kernel parameter blocks.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -275,12 +276,35 @@ std::vector<Group> plan_groups(int n, int TB, int chigh = kHighC) {
   return gs;
 }
 
-// Groups for the TMA passes: 32-amplitude (256-byte) segments when that
-// costs no extra group, 16-amplitude (128-byte) ones otherwise.
+// Groups for the TMA passes: 32-amplitude (256-byte state, 128-byte cost
+// rows) segments when that costs no extra group, 16-amplitude ones otherwise;
+// and within a 16-amplitude plan, every group whose new qubits fit the rows
+// of a 32-amplitude tile gets one (its cost rows then span 128 bytes, not 64;
+// 64-byte rows made the cost load the slowest part of the phase passes).
 std::vector<Group> tma_groups(int n, int TB) {
   std::vector<Group> g4 = plan_groups(n, TB, 4);
   std::vector<Group> g5 = plan_groups(n, TB, 5);
-  return g5.size() <= g4.size() ? g5 : g4;
+  if (g5.size() <= g4.size()) return g5;
+  const int rows5 = TB - 5;
+  for (Group &G : g4) {
+    if (!G.high || G.c != 4 || __builtin_popcount(G.rot) > rows5) continue;
+    // the group's new qubits: h + j - 4 for the set bits j of rot
+    int q0 = 1 << 30, q1 = -1;
+    for (int j = 4; j < TB; ++j)
+      if ((G.rot >> j) & 1u) {
+        q0 = std::min(q0, G.h + j - 4);
+        q1 = std::max(q1, G.h + j - 4);
+      }
+    if (q1 - q0 + 1 > rows5) continue;
+    const int h = q0 < n - rows5 ? q0 : n - rows5;
+    uint32_t rot = 0;
+    for (int j = 5; j < TB; ++j) {
+      const int q = h + j - 5;
+      if (q >= q0 && q <= q1) rot |= 1u << j;
+    }
+    G = Group{true, 5, h, rot};
+  }
+  return g4;
 }
 
 Geom make_geom(int n, const Group &G, int TB) {
