@@ -44,9 +44,9 @@ def parse():
     ap.add_argument("--cpu-sample-n", type=int, default=23,
                     help="n of the oracle sample timed for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--n", type=int, default=None,
+    ap.add_argument("--qubits", "--n", dest="n", type=int, default=None,
                     help="LABS size override (a smaller case for profiling; default n=30)")
-    ap.add_argument("--p", type=int, default=None,
+    ap.add_argument("--layers", "--p", dest="p", type=int, default=None,
                     help="layer-count override (default p=10)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=400)

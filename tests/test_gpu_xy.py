@@ -65,3 +65,29 @@ def test_xy_keeps_hamming_weight_on_gpu(Q):
     for k in range(n + 1):
         want = 0.5 if k in (5, 9) else 0.0
         assert abs(np.sum(np.abs(p[w == k]) ** 2) - want) < 2e-6
+
+
+@pytest.mark.parametrize("kind", ["f32", "u16"])
+def test_simulate_xy_other_cost_types(Q, kind):
+    # float32 costs take the computed phase, uint16 costs the digit tables
+    # read as 2-byte words
+    n = 15
+    if kind == "f32":
+        edges, w = I.maxcut_3reg(n + 1, graph_seed=6, weighted=True, weight_seed=7)
+        n = n + 1
+        f = oracle.maxcut_costs(n, edges, w)
+        fd = Q.maxcut_costs(n, edges, w, Q.COST_F32)
+        f = oracle.to_f32_rne(f).astype(float)
+    else:
+        f = oracle.labs_costs(n).astype(float)
+        fd = Q.labs_costs_u16(n)
+    stats = Q.cost_stats_compute(fd)
+    g, b = I.angles(2, 95, 0, 0.4), I.angles(2, 96)
+    psi0 = oracle.dicke(n, n // 2)
+    state = Q.dicke_state(n, n // 2)
+    state, out = Q.simulate_xy(fd, stats, g, b, state, Q.XY_RING)
+    ref = oracle.simulate_xy(n, f, g, b, psi0, 1)
+    got = dev_np(state).astype(np.complex128)
+    assert np.linalg.norm(got - ref) <= 2e-5 * np.linalg.norm(ref)
+    E = oracle.energy(n, ref, f)
+    assert abs(dev_np(out)[0] - E) <= 1e-5 * max(1.0, abs(E))
