@@ -276,35 +276,42 @@ std::vector<Group> plan_groups(int n, int TB, int chigh = kHighC) {
   return gs;
 }
 
-// Groups for the TMA passes: 32-amplitude (256-byte state, 128-byte cost
-// rows) segments when that costs no extra group, 16-amplitude ones otherwise;
-// and within a 16-amplitude plan, every group whose new qubits fit the rows
-// of a 32-amplitude tile gets one (its cost rows then span 128 bytes, not 64;
-// 64-byte rows made the cost load the slowest part of the phase passes).
+// Groups for the TMA passes: the widest segments (2^c contiguous amplitudes,
+// c = 5 or 4: 256/128-byte state rows, 128/64-byte int32 cost rows) that cost
+// no extra group; and within a plan whose HIGH groups have narrower segments,
+// every group whose new qubits fit the rows of a wider tile gets it (64-byte
+// cost rows made the cost load the slowest part of the phase passes).  c = 6
+// was measured slower (the 6 row qubits split unevenly over the two rounds).
+constexpr int kMaxSegBits = 5;
+
 std::vector<Group> tma_groups(int n, int TB) {
-  std::vector<Group> g4 = plan_groups(n, TB, 4);
-  std::vector<Group> g5 = plan_groups(n, TB, 5);
-  if (g5.size() <= g4.size()) return g5;
-  const int rows5 = TB - 5;
-  for (Group &G : g4) {
-    if (!G.high || G.c != 4 || __builtin_popcount(G.rot) > rows5) continue;
-    // the group's new qubits: h + j - 4 for the set bits j of rot
-    int q0 = 1 << 30, q1 = -1;
-    for (int j = 4; j < TB; ++j)
-      if ((G.rot >> j) & 1u) {
-        q0 = std::min(q0, G.h + j - 4);
-        q1 = std::max(q1, G.h + j - 4);
-      }
-    if (q1 - q0 + 1 > rows5) continue;
-    const int h = q0 < n - rows5 ? q0 : n - rows5;
-    uint32_t rot = 0;
-    for (int j = 5; j < TB; ++j) {
-      const int q = h + j - 5;
-      if (q >= q0 && q <= q1) rot |= 1u << j;
-    }
-    G = Group{true, 5, h, rot};
+  std::vector<Group> best = plan_groups(n, TB, 4);
+  for (int c = 5; c <= kMaxSegBits; ++c) {
+    std::vector<Group> g = plan_groups(n, TB, c);
+    if (g.size() <= best.size()) best = g;
   }
-  return g4;
+  for (Group &G : best) {
+    if (!G.high) continue;
+    int q0 = 1 << 30, q1 = -1;  // the group's new qubits: h + j - c for the set bits j of rot
+    for (int j = G.c; j < TB; ++j)
+      if ((G.rot >> j) & 1u) {
+        q0 = std::min(q0, G.h + j - G.c);
+        q1 = std::max(q1, G.h + j - G.c);
+      }
+    for (int c = kMaxSegBits; c > G.c; --c) {
+      const int rows = TB - c;
+      if (q1 - q0 + 1 > rows) continue;
+      const int h = q0 < n - rows ? q0 : n - rows;
+      uint32_t rot = 0;
+      for (int j = c; j < TB; ++j) {
+        const int q = h + j - c;
+        if (q >= q0 && q <= q1) rot |= 1u << j;
+      }
+      G = Group{true, c, h, rot};
+      break;
+    }
+  }
+  return best;
 }
 
 Geom make_geom(int n, const Group &G, int TB) {

@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
   __syncthreads();
 
   // 16-amplitude segments: the outer bits between the segments are view
-  // dimension 1; 32-amplitude segments (bit 4 is view dimension 1): dimension 2
+  // dimension 1; wider segments (bits 4.. are view dimension 1): dimension 2
   auto coords = [&](uint64_t T) {
     const int mid = (int)(T & ((1ull << midbits) - 1ull));
     TC c;
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
   __syncthreads();
 
   // 16-amplitude segments: the outer bits between the segments are view
-  // dimension 1; 32-amplitude segments (bit 4 is view dimension 1): dimension 2
+  // dimension 1; wider segments (bits 4.. are view dimension 1): dimension 2
   auto coords = [&](uint64_t T) {
     const int mid = (int)(T & ((1ull << midbits) - 1ull));
     TC c;
@@ -907,14 +907,14 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
   const cuuint64_t e = (cuuint64_t)esz;
   cuuint64_t dims[5], strides[4];
   cuuint32_t box[5];
-  if (c == 5) {
-    // 32 contiguous amplitudes as [16][2] (a swizzled box row is at most
-    // 128 bytes), then the outer bits 5..h-1, the rows, the rest
-    const int rows = tb - 5;
-    if (h < 5 || rows > 8 || n < h + rows) return cudaErrorInvalidValue;
-    const cuuint64_t d[5] = {16, 2, 1ull << (h - 5), 1ull << rows, 1ull << (n - h - rows)};
-    const cuuint64_t st[4] = {16 * e, 32 * e, (1ull << h) * e, (1ull << (h + rows)) * e};
-    const cuuint32_t bx[5] = {16, 2, 1, (cuuint32_t)(1u << rows), 1};
+  if (c >= 5) {
+    // 2^c contiguous amplitudes as [16][2^(c-4)] (a swizzled box row is at
+    // most 128 bytes), then the outer bits c..h-1, the rows, the rest
+    const int rows = tb - c;
+    if (c > 7 || h < c || rows < 1 || rows > 8 || n < h + rows) return cudaErrorInvalidValue;
+    const cuuint64_t d[5] = {16, 1ull << (c - 4), 1ull << (h - c), 1ull << rows, 1ull << (n - h - rows)};
+    const cuuint64_t st[4] = {16 * e, (1ull << c) * e, (1ull << h) * e, (1ull << (h + rows)) * e};
+    const cuuint32_t bx[5] = {16, (cuuint32_t)(1u << (c - 4)), 1, (cuuint32_t)(1u << rows), 1};
     for (int i = 0; i < 5; ++i) dims[i] = d[i], box[i] = bx[i];
     for (int i = 0; i < 4; ++i) strides[i] = st[i];
   } else {
@@ -1022,13 +1022,13 @@ static cudaError_t dispatch_bwd(const TmaBwdParams &P, cudaStream_t s, int nsm) 
 #endif
 
 cudaError_t QAOA_TMA_FN(launch_fwd_tma)(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm) {
-  if (P.c != 4 && P.c != 5) return cudaErrorInvalidValue;  // 16- or 32-amplitude segments
+  if (P.c < 4 || P.c > 6) return cudaErrorInvalidValue;  // 16- to 64-amplitude segments
   if (!P.psi || ((uintptr_t)P.psi & 15u)) return cudaErrorInvalidValue;
   return high ? dispatch_fwd<PlanTmaF13High>(P, s, nsm) : dispatch_fwd<PlanTmaF13Low>(P, s, nsm);
 }
 
 cudaError_t QAOA_TMA_FN(launch_bwd_tma)(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {
-  if (P.c != 4 && P.c != 5) return cudaErrorInvalidValue;  // 16- or 32-amplitude segments
+  if (P.c < 4 || P.c > 6) return cudaErrorInvalidValue;  // 16- to 64-amplitude segments
   if (!P.psi || !P.lam || ((uintptr_t)P.psi & 15u) || ((uintptr_t)P.lam & 15u))
     return cudaErrorInvalidValue;
   return high ? dispatch_bwd<PlanTmaB12High>(P, s, nsm) : dispatch_bwd<PlanTmaB12Low>(P, s, nsm);
