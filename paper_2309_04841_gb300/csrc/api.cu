@@ -258,7 +258,7 @@ struct Group {
 
 // LOW group + HIGH groups covering qubits [TB, n), TB - chigh per pass
 // (chigh passenger bits keep every global segment 2^chigh amplitudes long).
-std::vector<Group> plan_groups(int n, int TB, int chigh = kHighC) {
+std::vector<Group> plan_groups(int n, int TB, int chigh) {
   std::vector<Group> gs;
   gs.push_back(Group{false, TB, TB, (1u << TB) - 1u});
   const int span = TB - chigh;
@@ -504,7 +504,7 @@ qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa
   using Low = typename FwdTB<Real>::Low;
   using High = typename FwdTB<Real>::High;
   const int TB = Low::TB;
-  const std::vector<Group> gs = plan_groups(n, TB);
+  const std::vector<Group> gs = plan_groups(n, TB, kHighC);
   const std::vector<PassOp> ops = forward_schedule((int)gs.size(), p, init_plus != 0, d_out != nullptr);
   const int nsm = num_sms();
   if (d_out) CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
@@ -557,7 +557,7 @@ qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qao
   using Low = typename BwdTB<Real>::Low;
   using High = typename BwdTB<Real>::High;
   const int TB = Low::TB;
-  const std::vector<Group> gs = plan_groups(n, TB);
+  const std::vector<Group> gs = plan_groups(n, TB, kHighC);
   const std::vector<PassOp> ops = adjoint_schedule((int)gs.size(), p);
   const int nsm = num_sms();
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");

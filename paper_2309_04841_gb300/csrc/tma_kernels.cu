@@ -1,19 +1,20 @@
 // tma_kernels.cu -- complex64 passes streamed by the Tensor Memory Accelerator.
 //
-// Same math as pass_kernels.cu (Algorithm 1 rotations on a tile window, the
-// phase of Algorithm 3, energy/overlap, and the adjoint inner products), with
-// the data movement done by TMA:
-//   * a persistent CTA per SM: 8 compute warps + 1 producer warp;
-//   * the producer issues cp.async.bulk.tensor loads of the next tiles into
-//     a 2-stage shared-memory ring (mbarrier complete_tx), and bulk tensor
-//     stores of finished tiles back to HBM, so loads, stores and compute of
-//     neighbouring tiles overlap;
-//   * tiles land in shared memory with the TMA 128-byte swizzle; the compute
-//     rounds are laid out so that every shared-memory access of the state is
-//     bank-conflict free under that swizzle.
-// A tile is 2^TB amplitudes: 16 contiguous ones (128 B) times 2^(TB-4) rows at
-// qubits h.. (h = 4 for the contiguous LOW pass).  The tensor map views the
-// state as [16][2^(h-4)][256][2^(TB-12)][rest]; one box is one tile.
+// Algorithm 1 rotations on a tile window (in the twisted basis, packed fp32x2
+// FMA), the phase of Algorithm 3 (conflict-free digit tables), the fused
+// energy/overlap, and the adjoint inner products:
+//   * persistent CTAs, two per SM, 256 threads each, one tile buffer each;
+//   * thread 0 issues cp.async.bulk.tensor loads (mbarrier complete_tx) of the
+//     state tile (and the cost tile) with the TMA 128-byte swizzle; the
+//     compute rounds are laid out so that every shared-memory access of the
+//     state is bank-conflict free under that swizzle;
+//   * once the last round's data is in registers the buffer goes to the next
+//     tile's load, and the finished tile is stored from the registers with
+//     coalesced global stores while that load is in flight; the other CTA on
+//     the SM computes meanwhile.
+// A tile is 2^TB amplitudes: 2^c contiguous ones (c = 4..6) times 2^(TB-c)
+// rows at qubits h.. (the contiguous LOW tile for the low group).  The tensor
+// maps view the vectors as 5-D arrays so that one box is one tile.
 // Every wait on an mbarrier is bounded (about one second of %globaltimer);
 // on timeout the kernel records an error word and returns.
 #include <cuda.h>
