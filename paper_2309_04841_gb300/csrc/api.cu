@@ -282,15 +282,15 @@ std::vector<Group> plan_groups(int n, int TB, int chigh) {
 // every group whose new qubits fit the rows of a wider tile gets it (64-byte
 // cost rows made the cost load the slowest part of the phase passes).  c = 6
 // was measured slower (the 6 row qubits split unevenly over the two rounds).
+// With cmin = 3 (the adjoint), a plan with one group of 8-amplitude segments
+// (64-byte state rows, 9 new qubits) is taken where it saves a group: its
+// passes ran about 1.5x as long as 16-amplitude ones, and a second such group
+// (n = 30: rows 21..29) 2.7x, which loses against the extra group.
 constexpr int kMaxSegBits = 5;
 
-std::vector<Group> tma_groups(int n, int TB) {
-  std::vector<Group> best = plan_groups(n, TB, 4);
-  for (int c = 5; c <= kMaxSegBits; ++c) {
-    std::vector<Group> g = plan_groups(n, TB, c);
-    if (g.size() <= best.size()) best = g;
-  }
-  for (Group &G : best) {
+// every HIGH group whose new qubits fit the rows of a wider tile gets it
+void widen_groups(std::vector<Group> &gs, int n, int TB) {
+  for (Group &G : gs) {
     if (!G.high) continue;
     int q0 = 1 << 30, q1 = -1;  // the group's new qubits: h + j - c for the set bits j of rot
     for (int j = G.c; j < TB; ++j)
@@ -310,6 +310,21 @@ std::vector<Group> tma_groups(int n, int TB) {
       G = Group{true, c, h, rot};
       break;
     }
+  }
+}
+
+std::vector<Group> tma_groups(int n, int TB, int cmin) {
+  std::vector<Group> best = plan_groups(n, TB, 4);
+  for (int c = 5; c <= kMaxSegBits; ++c) {
+    std::vector<Group> g = plan_groups(n, TB, c);
+    if (g.size() <= best.size()) best = g;
+  }
+  widen_groups(best, n, TB);
+  if (cmin <= 3) {
+    std::vector<Group> g = plan_groups(n, TB, 3);
+    widen_groups(g, n, TB);
+    const auto narrow = std::count_if(g.begin(), g.end(), [](const Group &G) { return G.high && G.c == 3; });
+    if (g.size() < best.size() && narrow <= 1) best = g;
   }
   return best;
 }
@@ -585,7 +600,8 @@ qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qao
       P.s2s = (Real)-sin(bet[op.l2]);
       P.out_b2 = d_grad_b + op.l2;
     }
-    if (uses_lanes(P.s1) || uses_lanes(P.s2)) return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
+    if (uses_lanes(P.s1) || uses_lanes(P.s2))
+      return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
     P.init_lambda = op.init;
     P.partials = ws.partials;
     P.counter = ws.counter;
@@ -652,7 +668,7 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
   using Low = PlanTmaF13Low;
   using High = PlanTmaF13High;
   const int TB = Low::TB;
-  const std::vector<Group> gs = tma_groups(n, TB);
+  const std::vector<Group> gs = tma_groups(n, TB, 4);
   const std::vector<PassOp> ops = forward_schedule((int)gs.size(), p, init_plus != 0, d_out != nullptr);
   const int nsm = num_sms();
   if (d_out) CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
@@ -726,8 +742,10 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
   using Low = PlanTmaB12Low;
   using High = PlanTmaB12High;
   const int TB = Low::TB;
-  // 16- or 32-amplitude segments (8-amplitude ones halve the HBM efficiency)
-  const std::vector<Group> gs = tma_groups(n, TB);
+  // one group of 8-amplitude segments where that saves a group (n = 29:
+  // 12 + 9 + 8 qubits in three groups instead of four); a HIGH group with
+  // 8-amplitude segments rotates 9 tile bits, tile bit 3 as a lane bit
+  const std::vector<Group> gs = tma_groups(n, TB, 3);
   const std::vector<PassOp> ops = adjoint_schedule((int)gs.size(), p);
   const int nsm = num_sms();
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
@@ -739,7 +757,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
     const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
-    const int sw = 128;
+    const int sw = c == 3 ? 64 : 128;  // a 128-byte swizzle pads 64-byte box rows
     CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, sw), "tensor map (psi)");
     CK(make_tile_map(&P.map_lam, lam, n, TB, h, c, 8, sw), "tensor map (lambda)");
     P.psi = reinterpret_cast<float2 *>(state);
@@ -784,7 +802,8 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
       }
       P.out_b2 = d_grad_b + op.l2;
     }
-    if (uses_lanes(P.s1) || uses_lanes(P.s2)) return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
+    if ((uses_lanes(P.s1) || uses_lanes(P.s2)) && c != 3)
+      return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
     P.init_lambda = op.init;
     P.untwist = &op == &ops.back();
     P.partials = ws.partials;

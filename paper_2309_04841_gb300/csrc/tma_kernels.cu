@@ -163,11 +163,15 @@ __device__ __forceinline__ void rot_tw(float2 (&v)[1 << EB], uint32_t m, float t
 // Im <lambda| X_q |psi> of each pair, which in the twisted basis is
 // lambda_a . psi_b - lambda_b . psi_a (real dot products of the complex
 // components); the round's sum is weighted by wr (the squared scale the
-// stored vectors owe at this point).
-template <int EB>
+// stored vectors owe at this point).  With LANES, lm (at most one bit) names
+// a lane bit whose pairs sit in two lanes: each lane takes its partner's
+// values by shuffle, adds its half of the pair term and updates its own
+// element.  Every product of the round uses the vectors as they were before
+// the round's rotations.
+template <int EB, bool LANES>
 __device__ __forceinline__ void unrot_tw(float2 (&v)[1 << EB], float2 (&w)[1 << EB], uint32_t m,
-                                         float tau, int form, float wr, float &acc) {
-  if (m == 0u) return;
+                                         uint32_t lm, float tau, int form, float wr, float &acc) {
+  if (m == 0u && (!LANES || lm == 0u)) return;
   // two accumulator pairs (by register parity) halve the dependency chains
   float2 pp[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, pm[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
 #pragma unroll
@@ -182,7 +186,32 @@ __device__ __forceinline__ void unrot_tw(float2 (&v)[1 << EB], float2 (&w)[1 << 
         }
     }
   const float2 sp = __fadd2_rn(pp[0], pp[1]), sm = __fadd2_rn(pm[0], pm[1]);
-  acc = fmaf((sp.x + sp.y) - (sm.x + sm.y), wr, acc);
+  float lane_term = 0.f;
+  if constexpr (LANES) {
+    if (lm != 0u) {
+      const int lb = __ffs((int)lm) - 1;
+      const float sg = ((threadIdx.x >> lb) & 1u) ? -1.f : 1.f;  // -1: the pair's upper element
+      const float2 st = f2(sg * tau, sg * tau), tt = f2(tau, tau);
+      float2 q = f2(0.f, 0.f);
+#pragma unroll
+      for (int r = 0; r < (1 << EB); ++r) {
+        const float2 pv = f2(__shfl_xor_sync(0xffffffffu, v[r].x, 1 << lb),
+                             __shfl_xor_sync(0xffffffffu, v[r].y, 1 << lb));
+        const float2 pw = f2(__shfl_xor_sync(0xffffffffu, w[r].x, 1 << lb),
+                             __shfl_xor_sync(0xffffffffu, w[r].y, 1 << lb));
+        q = __ffma2_rn(w[r], pv, q);
+        if (form == 0) {  // (a, b) <- (a + t b, b - t a)
+          v[r] = __ffma2_rn(st, pv, v[r]);
+          w[r] = __ffma2_rn(st, pw, w[r]);
+        } else {  // (a, b) <- (u a + b, u b - a)
+          v[r] = __ffma2_rn(tt, v[r], f2(sg * pv.x, sg * pv.y));
+          w[r] = __ffma2_rn(tt, w[r], f2(sg * pw.x, sg * pw.y));
+        }
+      }
+      lane_term = sg * (q.x + q.y);
+    }
+  }
+  acc = fmaf((sp.x + sp.y) - (sm.x + sm.y) + lane_term, wr, acc);
   rot_tw<EB>(v, m, tau, form);
   rot_tw<EB>(w, m, tau, form);
 }
@@ -467,7 +496,8 @@ __device__ __forceinline__ Lay layout(uint32_t tile_elems, bool two, bool cost) 
 // registers: tile offset t of tile T is amplitude
 //   x = (t & (2^c - 1)) | (mid << c) | ((t >> c) << h) | (top << (h + TB - c)),
 // mid / top the low h - c / remaining bits of T.  In every round the 32 lanes
-// of a warp cover whole 128-byte segments, so the stores are coalesced.
+// of a warp cover whole 2^c-amplitude segments (c >= 3: 64 bytes or more),
+// so the stores are coalesced.
 template <class PL, int R>
 __device__ __forceinline__ void stg_round(const float2 (&v)[PL::NREG], float2 *g, uint64_t T,
                                           int h, int c) {
@@ -552,13 +582,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
   }
   __syncthreads();
 
-  // 16-amplitude segments: the outer bits between the segments are view
+  // 8- or 16-amplitude segments: the outer bits between the segments are view
   // dimension 1; wider segments (bits 4.. are view dimension 1): dimension 2
   auto coords = [&](uint64_t T) {
     const int mid = (int)(T & ((1ull << midbits) - 1ull));
     TC c;
-    c.x1 = P.c == 4 ? mid : 0;
-    c.x2 = P.c == 4 ? 0 : mid;
+    c.x1 = P.c <= 4 ? mid : 0;
+    c.x2 = P.c <= 4 ? 0 : mid;
     c.x4 = (int)(T >> midbits);
     return c;
   };
@@ -714,9 +744,14 @@ __device__ __forceinline__ void unphase_round(float2 (&v)[PL::NREG], float2 (&w)
   }
 }
 
-template <class PL, int K>
+// SW: the state tiles' TMA swizzle, 128 for 16- to 64-amplitude segments, 64
+// for 8-amplitude ones (whose 64-byte box rows a 128-byte swizzle would pad
+// to 128 bytes in shared memory); the latter rotate tile bit 3, a lane bit in
+// both rounds of the two-round plan, by shuffles.
+template <class PL, int K, int SW>
 __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
-  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, SW = 128;
+  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB;
+  constexpr bool LN = SW == 64;
   constexpr bool PH = (K & kPH) != 0, H2 = (K & kH2) != 0, INIT = (K & kINIT) != 0;
   constexpr bool need_cost = PH || INIT;
   constexpr int RS = H2 ? 0 : NR - 1;  // the round the tiles are stored from
@@ -741,13 +776,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
   }
   __syncthreads();
 
-  // 16-amplitude segments: the outer bits between the segments are view
+  // 8- or 16-amplitude segments: the outer bits between the segments are view
   // dimension 1; wider segments (bits 4.. are view dimension 1): dimension 2
   auto coords = [&](uint64_t T) {
     const int mid = (int)(T & ((1ull << midbits) - 1ull));
     TC c;
-    c.x1 = P.c == 4 ? mid : 0;
-    c.x2 = P.c == 4 ? 0 : mid;
+    c.x1 = P.c <= 4 ? mid : 0;
+    c.x2 = P.c <= 4 ? 0 : mid;
     c.x4 = (int)(T >> midbits);
     return c;
   };
@@ -803,17 +838,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
       lds_round<PL, 0, SW>(w, bw);
     }
     float a1 = 0.f, ag = 0.f, a2 = 0.f;
-    unrot_tw<EB>(v, w, P.s1.m[0], P.tau1, P.form1, P.w1[0], a1);
+    unrot_tw<EB, LN>(v, w, P.s1.m[0], P.s1.lm[0], P.tau1, P.form1, P.w1[0], a1);
     if constexpr (INIT && early_cost)
       xp_pair<PL, 0, 1, SW>(v, w, bv, bw, [&] { cost_next(T); });
     else
       xp_pair<PL, 0, 1, SW>(v, w, bv, bw, NoHook());
     if constexpr (NR == 2 && !PH && !H2) release(T);
-    unrot_tw<EB>(v, w, P.s1.m[1], P.tau1, P.form1, P.w1[1], a1);
+    unrot_tw<EB, LN>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
     if constexpr (NR == 3) {
       xp_pair<PL, 1, 2, SW>(v, w, bv, bw, NoHook());
       if constexpr (!PH && !H2) release(T);
-      unrot_tw<EB>(v, w, P.s1.m[2], P.tau1, P.form1, P.w1[2], a1);
+      unrot_tw<EB, LN>(v, w, P.s1.m[2], P.s1.lm[2], P.tau1, P.form1, P.w1[2], a1);
     }
     if constexpr (PH) {
       // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
@@ -827,13 +862,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
       if constexpr (!H2) release(T);
     }
     if constexpr (H2) {
-      unrot_tw<EB>(v, w, P.s2.m[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
+      unrot_tw<EB, LN>(v, w, P.s2.m[NR - 1], P.s2.lm[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
       if constexpr (NR == 3) {
         if constexpr (PH && early_cost)
           xp_pair<PL, 2, 1, SW>(v, w, bv, bw, [&] { cost_next(T); });
         else
           xp_pair<PL, 2, 1, SW>(v, w, bv, bw, NoHook());
-        unrot_tw<EB>(v, w, P.s2.m[1], P.tau2, P.form2, P.w2[1], a2);
+        unrot_tw<EB, LN>(v, w, P.s2.m[1], P.s2.lm[1], P.tau2, P.form2, P.w2[1], a2);
         xp_pair<PL, 1, 0, SW>(v, w, bv, bw, NoHook());
       } else if constexpr (PH && early_cost) {
         xp_pair<PL, 1, 0, SW>(v, w, bv, bw, [&] { cost_next(T); });
@@ -841,7 +876,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
         xp_pair<PL, 1, 0, SW>(v, w, bv, bw, NoHook());
       }
       release(T);
-      unrot_tw<EB>(v, w, P.s2.m[0], P.tau2, P.form2, P.w2[0], a2);
+      unrot_tw<EB, LN>(v, w, P.s2.m[0], P.s2.lm[0], P.tau2, P.form2, P.w2[0], a2);
     }
     if (P.untwist) {
       // psi back to the standard basis (lambda is scratch from here on)
@@ -967,10 +1002,10 @@ static cudaError_t launch_fwd_tma_t(const TmaFwdParams &P, cudaStream_t s, int n
   return cudaGetLastError();
 }
 
-template <class PL, int K>
+template <class PL, int K, int SW>
 static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int nsm) {
   const size_t smem = smem_bytes(PL::TB, true, (K & (kPH | kINIT)) != 0);
-  auto kern = k_bwd_tma<PL, K>;
+  auto kern = k_bwd_tma<PL, K, SW>;
   static int nb = 0;
   if (nb == 0) {
     const size_t mx = smem_bytes(PL::TB, true, true);
@@ -1002,16 +1037,16 @@ static cudaError_t dispatch_fwd(const TmaFwdParams &P, cudaStream_t s, int nsm) 
   }
 }
 
-template <class PL>
+template <class PL, int SW>
 static cudaError_t dispatch_bwd(const TmaBwdParams &P, cudaStream_t s, int nsm) {
-  const bool h2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2]) != 0;
+  const bool h2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2] | P.s2.lm[0] | P.s2.lm[1] | P.s2.lm[2]) != 0;
   const int k = (P.has_phase ? kPH : 0) | (h2 ? kH2 : 0) | (P.init_lambda ? kINIT : 0);
   switch (k) {  // the kinds the adjoint schedules produce
-    case 0: return launch_bwd_tma_t<PL, 0>(P, s, nsm);
-    case kINIT: return launch_bwd_tma_t<PL, kINIT>(P, s, nsm);
-    case kPH | kH2: return launch_bwd_tma_t<PL, kPH | kH2>(P, s, nsm);
-    case kPH: return launch_bwd_tma_t<PL, kPH>(P, s, nsm);
-    case kPH | kINIT: return launch_bwd_tma_t<PL, kPH | kINIT>(P, s, nsm);
+    case 0: return launch_bwd_tma_t<PL, 0, SW>(P, s, nsm);
+    case kINIT: return launch_bwd_tma_t<PL, kINIT, SW>(P, s, nsm);
+    case kPH | kH2: return launch_bwd_tma_t<PL, kPH | kH2, SW>(P, s, nsm);
+    case kPH: return launch_bwd_tma_t<PL, kPH, SW>(P, s, nsm);
+    case kPH | kINIT: return launch_bwd_tma_t<PL, kPH | kINIT, SW>(P, s, nsm);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1029,10 +1064,15 @@ cudaError_t QAOA_TMA_FN(launch_fwd_tma)(const TmaFwdParams &P, bool high, cudaSt
 }
 
 cudaError_t QAOA_TMA_FN(launch_bwd_tma)(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {
-  if (P.c < 4 || P.c > 6) return cudaErrorInvalidValue;  // 16- to 64-amplitude segments
+  if (P.c < 3 || P.c > 6 || (P.c == 3 && !high)) return cudaErrorInvalidValue;  // 8- to 64-amplitude segments
   if (!P.psi || !P.lam || ((uintptr_t)P.psi & 15u) || ((uintptr_t)P.lam & 15u))
     return cudaErrorInvalidValue;
-  return high ? dispatch_bwd<PlanTmaB12High>(P, s, nsm) : dispatch_bwd<PlanTmaB12Low>(P, s, nsm);
+  for (int r = 0; r < 3; ++r)  // lane rotations: one lane bit per round, 8-amplitude segments only
+    if ((P.c != 3 && (P.s1.lm[r] | P.s2.lm[r]) != 0) || __builtin_popcount(P.s1.lm[r]) > 1 ||
+        __builtin_popcount(P.s2.lm[r]) > 1)
+      return cudaErrorInvalidValue;
+  if (P.c == 3) return dispatch_bwd<PlanTmaB12High, 64>(P, s, nsm);
+  return high ? dispatch_bwd<PlanTmaB12High, 128>(P, s, nsm) : dispatch_bwd<PlanTmaB12Low, 128>(P, s, nsm);
 }
 
 }  // namespace qaoa

@@ -42,6 +42,28 @@ def test_grad_vs_oracle_labs(Q, n, p, st, tol):
     assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < tol
 
 
+@pytest.mark.parametrize("cost", ["i32", "f32"])
+@pytest.mark.parametrize("n,p", [(21, 3), (21, 1)])
+def test_grad_8_amplitude_segments_vs_oracle(Q, cost, n, p):
+    # n = 21: the adjoint's HIGH group takes qubits 12..20 in 8-amplitude
+    # segments (one group instead of two), tile bit 3 rotated across lanes;
+    # int32 and float32 cost tiles (LABS energies, scaled and perturbed for
+    # the latter)
+    f = oracle.labs_costs(n).astype(float)
+    if cost == "i32":
+        fd = Q.labs_costs(n)
+    else:
+        f = (0.37 * f + I.uniform(5, 1 << n, -0.5, 0.5)).astype(np.float32).astype(float)
+        fd = torch().tensor(f.astype(np.float32), device="cuda")
+    stats = Q.cost_stats_compute(fd)
+    g = I.angles(p, 40 + n, 0, 0.2)
+    b = I.angles(p, 41 + n)
+    out = dev_np(Q.grad(fd, stats, g, b))
+    E, dg, db = oracle.grad(n, f, g, b)
+    assert abs(out[0] - E) <= 1e-5 * max(1.0, abs(E))
+    assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < 1e-4
+
+
 @pytest.mark.parametrize("n,p", [(10, 5), (16, 6)])
 def test_grad_vs_oracle_weighted_maxcut(Q, n, p):
     w = I.workload("maxcut3w28_p40", n=n)
@@ -108,6 +130,25 @@ def test_grad_fullsize_directional_fd(Q, name):
     dd = (4 * fd2 - fd1) / 3
     T.cuda.empty_cache()
     assert abs(np.dot(grad, v) - dd) <= 1e-4 * np.linalg.norm(grad)
+
+
+@pytest.mark.parametrize("n", [29, 30])
+def test_grad_c64_vs_c128_fullsize(Q, n):
+    # n = 29, 30: the complex64 adjoint runs 8-amplitude segments in one or
+    # both HIGH groups; every component against the complex128 adjoint (whose
+    # own parity with the oracle is checked at n <= 16)
+    w = I.workload("labs30_p10", n=n)
+    fd = gpu_costs(w)
+    stats = Q.cost_stats_compute(fd)
+    g, b = I.angles(w["p"], w["gamma_seed"], 0, w["ghi"]), I.angles(w["p"], w["beta_seed"])
+    T = torch()
+    o64 = dev_np(Q.grad(fd, stats, g, b, state_type=Q.C64))
+    T.cuda.empty_cache()
+    o128 = dev_np(Q.grad(fd, stats, g, b, state_type=Q.C128))
+    T.cuda.empty_cache()
+    p = w["p"]
+    assert abs(o64[0] - o128[0]) <= 1e-5 * abs(o128[0])
+    assert rel(o64[2:2 + 2 * p], o128[2:2 + 2 * p]) < 1e-4
 
 
 def test_autograd_function(Q):

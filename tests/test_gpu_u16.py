@@ -52,7 +52,8 @@ def test_convert_rejects_out_of_range(Q):
     assert e.value.status == 3  # QAOA_ERR_OVERFLOW
 
 
-@pytest.mark.parametrize("n,st", [(10, "c64"), (16, "c64"), (22, "c64"), (25, "c64"), (16, "c128")])
+@pytest.mark.parametrize("n,st", [(10, "c64"), (16, "c64"), (21, "c64"), (22, "c64"), (25, "c64"),
+                                  (16, "c128")])
 def test_simulate_and_grad_match_int32_bit_for_bit(Q, n, st):
     T = torch()
     stype = Q.C64 if st == "c64" else Q.C128
