@@ -50,6 +50,7 @@ def parse():
                     help="layer-count override (default p=10)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=400)
+    ap.add_argument("--serving-full-requests", type=int, default=32)
     return ap.parse_args()
 
 
@@ -397,7 +398,7 @@ def run_ours(a, ws, rank, local):
 
 # ------------------------------------------------------------ serving
 
-def serving_bench(count=400, nmin=16, nmax=26):
+def serving_bench(count=400, nmin=16, nmax=26, loads=(0.5, 0.8, 0.95), graphs_per_n=4):
     """Serving loop vs the plain per-request path on one request stream."""
     import numpy as np
     import torch
@@ -405,7 +406,7 @@ def serving_bench(count=400, nmin=16, nmax=26):
     from paper_2309_04841_gb300 import inputs as I
     from paper_2309_04841_gb300 import qaoa as Q
 
-    reqs = I.serving_stream(count, nmin=nmin, nmax=nmax)
+    reqs = I.serving_stream(count, nmin=nmin, nmax=nmax, graphs_per_n=graphs_per_n)
     # plain path: one qaoa_grad after another on one stream, cost vectors cached
     cache = {}
     service = []
@@ -474,12 +475,13 @@ def serving_bench(count=400, nmin=16, nmax=26):
                 "server_p50_ms": pct(lat, 0.5), "server_p99_ms": pct(lat, 0.99),
                 "plain_p50_ms": pct(plat, 0.5), "plain_p99_ms": pct(plat, 0.99)}
 
-    sweep = [open_loop(x) for x in (0.5, 0.8, 0.95)]
-    mid = sweep[1]
+    sweep = [open_loop(x) for x in loads]
+    mid = sweep[len(sweep) // 2]
     return {"requests": count,
             "recipe": (f"objective+gradient requests, n ~ U{{{nmin}..{nmax}}} (MaxCut rounded up to even), "
-                       "p ~ U{1..40}, LABS or MaxCut 3-regular 50/50 (4 graphs per n), complex64; "
-                       "Poisson arrivals at 0.5 / 0.8 / 0.95 x the saturated server throughput"),
+                       f"p ~ U{{1..40}}, LABS or MaxCut 3-regular 50/50 ({graphs_per_n} graphs per n), complex64; "
+                       "Poisson arrivals at " + " / ".join(f"{x:g}" for x in loads)
+                       + " x the saturated server throughput; arena " + f"{arena / 2**30:.0f} GiB"),
             "server": {"evals_per_s_saturated": sat_tput, "arrival_rate_per_s": mid["arrival_rate_per_s"],
                        "p50_ms": mid["server_p50_ms"], "p99_ms": mid["server_p99_ms"]},
             "plain_per_request": {"evals_per_s": plain_tput, "p50_ms": mid["plain_p50_ms"],
@@ -532,6 +534,10 @@ def main():
         line["clocks"] = clocks
         if not a.no_serving:
             line["serving"] = serving_bench(a.serving_requests)
+            # the full size range, up to n = 32 (32 GiB state + 32 GiB lambda
+            # + 16 GiB costs), admitted by footprint
+            line["serving_full_range"] = serving_bench(a.serving_full_requests, 16, 32, loads=(0.8,),
+                                                       graphs_per_n=1)
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(a.cpu_sample_n, line["config"]["p"],
                                                 line["config"]["n"])
