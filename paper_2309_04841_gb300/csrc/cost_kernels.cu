@@ -7,6 +7,9 @@
 // the vector is written to HBM exactly once.  Term data sits in the kernel
 // parameter block (constant bank): every thread of a warp reads the same
 // term, which the constant cache broadcasts.
+#include <climits>
+#include <type_traits>
+
 #include "qaoa_common.cuh"
 #include "kernels.h"
 
@@ -142,21 +145,55 @@ __device__ __forceinline__ MinMaxCnt mmc_join(MinMaxCnt a, MinMaxCnt b) {
 // merges them in block order.  out: [f_min, f_max, n_min, step bits], where
 // step bits = OR over x of (f[x] - f[0]) for int32 costs (0 otherwise): its
 // lowest set bit is the largest power of two dividing every f[x] - f_min.
+// One thread's min / max / count-of-min over its elements in the cost's own
+// type (integer compares for integer costs, no float64 work per element);
+// loads are issued 8 at a time so that enough bytes are in flight.
+template <typename T, typename L>
+__device__ __forceinline__ MinMaxCnt mmc_scan(const T *c, uint64_t N, L mn_init, L mx_init, uint32_t &bits,
+                                              T f0, bool want_bits) {
+  L mn = mn_init, mx = mx_init;
+  uint32_t cnt = 0u;
+  const uint64_t stride = (uint64_t)gridDim.x * 256ull;
+  auto take = [&](L f) {
+    if (f < mn) {
+      mn = f;
+      cnt = 0u;
+    }
+    cnt += f == mn ? 1u : 0u;
+    mx = f > mx ? f : mx;
+    if (want_bits) bits |= (uint32_t)(int)f - (uint32_t)(int)f0;  // modulo 2^32
+  };
+  uint64_t x0 = blockIdx.x * 256ull + threadIdx.x;
+  for (; x0 + 7 * stride < N; x0 += 8 * stride) {  // whole batches: 8 loads in flight
+    T v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __ldg(c + x0 + k * stride);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) take((L)v[k]);
+  }
+  for (; x0 < N; x0 += stride) take((L)__ldg(c + x0));
+  MinMaxCnt a = {(double)mn, (double)mx, (double)cnt};
+  if (cnt == 0u) a = {INFINITY, -INFINITY, 0.0};
+  return a;
+}
+
 __global__ void __launch_bounds__(256) k_cost_stats(int n, const void *cost, int kind,
                                                    double *partials, unsigned *counter,
                                                    double *out) {
   const uint64_t N = 1ull << n;
-  MinMaxCnt a = {INFINITY, -INFINITY, 0.0};
+  MinMaxCnt a;
   uint32_t bits = 0u;
-  const int *ci = reinterpret_cast<const int *>(cost);
-  const unsigned short *cu = reinterpret_cast<const unsigned short *>(cost);
-  const int f0 = kind == kCostI32 ? __ldg(ci) : kind == kCostU16 ? (int)__ldg(cu) : 0;
-  for (uint64_t x = blockIdx.x * 256ull + threadIdx.x; x < N; x += (uint64_t)gridDim.x * 256ull) {
-    const double f = cost_at(cost, kind, x);
-    MinMaxCnt b = {f, f, 1.0};
-    a = mmc_join(a, b);
-    if (kind == kCostI32) bits |= (uint32_t)(__ldg(ci + x) - f0);
-    if (kind == kCostU16) bits |= (uint32_t)((int)__ldg(cu + x) - f0);
+  if (kind == kCostI32) {
+    const int *ci = reinterpret_cast<const int *>(cost);
+    a = mmc_scan<int, int>(ci, N, INT_MAX, INT_MIN, bits, __ldg(ci), true);
+  } else if (kind == kCostU16) {
+    const unsigned short *cu = reinterpret_cast<const unsigned short *>(cost);
+    a = mmc_scan<unsigned short, int>(cu, N, INT_MAX, INT_MIN, bits, __ldg(cu), true);
+  } else if (kind == kCostF32) {
+    a = mmc_scan<float, float>(reinterpret_cast<const float *>(cost), N, INFINITY, -INFINITY, bits, 0.f, false);
+  } else {
+    a = mmc_scan<double, double>(reinterpret_cast<const double *>(cost), N, INFINITY, -INFINITY, bits, 0.0,
+                                 false);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -207,8 +244,166 @@ __global__ void __launch_bounds__(256) k_cost_stats(int n, const void *cost, int
   }
 }
 
+// Float-float arithmetic for the complex64 reduction: every product exact
+// (FMA), sums to about 2^-47 relative.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+struct FFs {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float h, float l) {
+    float s, e;
+    two_sum(hi, h, s, e);
+    e += lo + l;
+    hi = s + e;
+    lo = e - (hi - s);
+  }
+};
+
+// Cost value as an unevaluated sum fh + fl of floats (exact for int32,
+// uint16 and float32 costs; float64 ones to about 2^-48), and whether it is
+// the minimum (compared in the cost's own type).
+template <int KIND>
+struct CostFF {
+  using W = typename std::conditional<KIND == kCostI32, int,
+            typename std::conditional<KIND == kCostU16, unsigned short,
+            typename std::conditional<KIND == kCostF32, float, double>::type>::type>::type;
+  __device__ __forceinline__ static void split(W w, long long fmin_i, double fmin, float &fh, float &fl,
+                                               bool &at_min) {
+    if constexpr (KIND == kCostI32) {
+      fh = (float)w;
+      fl = (w < (1 << 24) && w > -(1 << 24)) ? 0.f : (float)((long long)w - (long long)fh);
+      at_min = w == fmin_i;
+    } else if constexpr (KIND == kCostU16) {
+      fh = (float)w;
+      fl = 0.f;
+      at_min = (int)w == fmin_i;
+    } else if constexpr (KIND == kCostF32) {
+      fh = w;
+      fl = 0.f;
+      at_min = w == (float)fmin;
+    } else {
+      fh = (float)w;
+      fl = (float)(w - (double)fh);
+      at_min = w == fmin;
+    }
+  }
+};
+
 // Standalone sum_x |psi_x|^2 f_x and sum_{f_x = fmin} |psi_x|^2 (Sec. 3.1,
-// Sec. 4): float64 accumulation, per-block partials merged in block order.
+// Sec. 4) of a complex64 state without float64 work per element: |psi_x|^2
+// and its product with f_x formed exactly as float pairs, summed with the
+// exact error of every add kept over runs of 32 elements (loads issued 8 at a
+// time, two interleaved chains), each run's sum added in float64.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_expect_c64(int n, const float2 *psi, const void *cost,
+                                                   double fmin, double *partials, unsigned *counter,
+                                                   double *out, int which) {
+  using W = typename CostFF<KIND>::W;
+  const W *cw = reinterpret_cast<const W *>(cost);
+  const uint64_t N = 1ull << n, stride = (uint64_t)gridDim.x * 256ull;
+  const long long fmin_i = (long long)fmin;
+  double e = 0.0, o = 0.0;
+  // energy chain: the high parts summed in float with the exact rounding error
+  // of every add (two_sum) collected, with the low parts, in a second float;
+  // read out as sum + low in float64 (only the add into sum is on the chain)
+  struct Chain {
+    float sum = 0.f, low = 0.f;
+    __device__ __forceinline__ void add(float q1, float q2) {
+      float t, err;
+      two_sum(sum, q1, t, err);
+      low += err + q2;
+      sum = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)sum + (double)low; }
+  };
+  auto take = [&](float2 v, W w, Chain &ce, FFs &fo) {
+    const float a1 = v.x * v.x, a2 = fmaf(v.x, v.x, -a1);
+    const float b1 = v.y * v.y, b2 = fmaf(v.y, v.y, -b1);
+    float p1, p2;
+    two_sum(a1, b1, p1, p2);
+    p2 += a2 + b2;  // |psi_x|^2 = p1 + p2
+    float fh, fl;
+    bool at_min;
+    CostFF<KIND>::split(w, fmin_i, fmin, fh, fl, at_min);
+    const float q1 = p1 * fh;
+    const float q2 = fmaf(p1, fh, -q1) + fmaf(p1, fl, p2 * fh);
+    ce.add(q1, q2);
+    if (at_min) fo.add(p1, p2);
+  };
+  uint64_t x0 = blockIdx.x * 256ull + threadIdx.x;
+  for (; x0 + 31 * stride < N; x0 += 32 * stride) {  // whole runs of 32, 8 loads in flight
+    Chain ce[2];  // two energy chains, so that their adds overlap
+    FFs fo;
+    for (int b = 0; b < 4; ++b) {
+      const uint64_t xb = x0 + 8 * b * stride;
+      float2 v[8];
+      W w[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        v[k] = __ldg(psi + xb + k * stride);
+        w[k] = __ldg(cw + xb + k * stride);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) take(v[k], w[k], ce[k & 1], fo);
+    }
+    e += ce[0].value() + ce[1].value();
+    o += (double)fo.hi + (double)fo.lo;
+  }
+  {
+    Chain ce;  // the rest: fewer than 32 elements
+    FFs fo;
+    for (; x0 < N; x0 += stride) take(__ldg(psi + x0), __ldg(cw + x0), ce, fo);
+    e += ce.value();
+    o += (double)fo.hi + (double)fo.lo;
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    e += __shfl_down_sync(0xffffffffu, e, s);
+    o += __shfl_down_sync(0xffffffffu, o, s);
+  }
+  __shared__ double se[8], so[8];
+  __shared__ int am_last;
+  if ((threadIdx.x & 31) == 0) {
+    se[threadIdx.x >> 5] = e;
+    so[threadIdx.x >> 5] = o;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double te = 0.0, to = 0.0;
+    for (int i = 0; i < 8; ++i) {
+      te += se[i];
+      to += so[i];
+    }
+    partials[blockIdx.x * 2] = te;
+    partials[blockIdx.x * 2 + 1] = to;
+    __threadfence();
+    am_last = (atomicAdd(counter, 1u) == gridDim.x - 1u);
+  }
+  __syncthreads();
+  if (am_last && threadIdx.x == 0) {
+    __threadfence();
+    double te = 0.0, to = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+      te += __ldcg(partials + b * 2);
+      to += __ldcg(partials + b * 2 + 1);
+    }
+    if (which == 2) {
+      out[0] = te;
+      out[1] = to;
+    } else {
+      out[0] = which == 0 ? te : to;
+    }
+    *counter = 0u;
+  }
+}
+
+// Standalone sum_x |psi_x|^2 f_x and sum_{f_x = fmin} |psi_x|^2 (Sec. 3.1,
+// Sec. 4) of a complex128 state: float64 accumulation, per-block partials
+// merged in block order.
 template <typename C2>
 __global__ void __launch_bounds__(256) k_expect(int n, const C2 *psi, const void *cost, int kind,
                                                double fmin, double *partials, unsigned *counter,
@@ -358,8 +553,14 @@ cudaError_t launch_expect(int n, const void *psi, bool c128, const void *cost, i
     k_expect<double2><<<reduce_grid(n, nsm), 256, 0, s>>>(
         n, reinterpret_cast<const double2 *>(psi), cost, kind, fmin, partials, counter, out, which);
   else
-    k_expect<float2><<<reduce_grid(n, nsm), 256, 0, s>>>(
-        n, reinterpret_cast<const float2 *>(psi), cost, kind, fmin, partials, counter, out, which);
+  {
+    const float2 *p = reinterpret_cast<const float2 *>(psi);
+    const unsigned g = reduce_grid(n, nsm);
+    if (kind == kCostI32) k_expect_c64<kCostI32><<<g, 256, 0, s>>>(n, p, cost, fmin, partials, counter, out, which);
+    else if (kind == kCostU16) k_expect_c64<kCostU16><<<g, 256, 0, s>>>(n, p, cost, fmin, partials, counter, out, which);
+    else if (kind == kCostF32) k_expect_c64<kCostF32><<<g, 256, 0, s>>>(n, p, cost, fmin, partials, counter, out, which);
+    else k_expect_c64<kCostF64><<<g, 256, 0, s>>>(n, p, cost, fmin, partials, counter, out, which);
+  }
   return cudaGetLastError();
 }
 

@@ -146,8 +146,20 @@ __device__ __forceinline__ uint64_t xy_index(const XyPass &P, uint64_t T, uint32
          (top << (P.h + P.tb - P.c));
 }
 
+// Registers per thread for the next tile's amplitudes (complex64; tiles of
+// up to 2^12 amplitudes over 256 threads, two neighbours per load).
+constexpr int kXyPrefetchPairs = (1 << kXyMaxTb) / 512;
+
 template <typename C2>
-__global__ void __launch_bounds__(256) k_xy_tile(const __grid_constant__ XyPass P) {
+__device__ __forceinline__ C2 xy_phased(const XyPass &P, const float2 *tab, bool table, C2 v, uint64_t x) {
+  return table ? xmul(v, xy_phase_tab(P, tab, v, x)) : xmul(v, xy_phase(P, v, x));
+}
+
+// PF (complex64): the next tile's amplitudes are loaded into registers while
+// the gates run on the current one in shared memory; otherwise the tile is
+// loaded just before its gates.
+template <typename C2, bool PF>
+__global__ void __launch_bounds__(256, PF ? 3 : 1) k_xy_tile(const __grid_constant__ XyPass P) {
   using R = typename XyR<C2>::R;
   extern __shared__ __align__(16) unsigned char xy_smem[];
   C2 *s = reinterpret_cast<C2 *>(xy_smem);
@@ -161,26 +173,51 @@ __global__ void __launch_bounds__(256) k_xy_tile(const __grid_constant__ XyPass 
     for (int i = threadIdx.x; i < P.ph.nent * kPhaseCopies; i += blockDim.x) tab[i] = P.ph.d[i >> 4];
     __syncthreads();
   }
+  // pairs of neighbouring amplitudes (tile bit 0 is qubit 0, c >= 1): one
+  // 16-byte load per complex64 pair; thread tid holds offsets 2 (tid + 256 i)
+  C2 r[PF ? 2 * kXyPrefetchPairs : 1];
+  auto load_regs = [&](uint64_t T) {
+    if constexpr (PF) {
+#pragma unroll
+      for (int i = 0; i < kXyPrefetchPairs; ++i) {
+        const uint32_t t = 2 * (threadIdx.x + 256u * i);
+        if (t < TE) ld2(psi + xy_index(P, T, t), r[2 * i], r[2 * i + 1]);
+      }
+    }
+  };
+  if (blockIdx.x < P.ntiles) load_regs(blockIdx.x);
   for (uint64_t T = blockIdx.x; T < P.ntiles; T += gridDim.x) {
-    // pairs of neighbouring amplitudes (tile bit 0 is qubit 0, c >= 1): one
-    // 16-byte load per complex64 pair
-    for (uint32_t t = 2 * threadIdx.x; t < TE; t += 2 * blockDim.x) {
-      const uint64_t x = xy_index(P, T, t);  // even
-      C2 v0, v1;
-      ld2(psi + x, v0, v1);
-      if (P.has_phase) {
-        if (table) {
-          v0 = xmul(v0, xy_phase_tab(P, tab, v0, x));
-          v1 = xmul(v1, xy_phase_tab(P, tab, v1, x + 1));
-        } else {
-          v0 = xmul(v0, xy_phase(P, v0, x));
-          v1 = xmul(v1, xy_phase(P, v1, x + 1));
+    if constexpr (PF) {
+#pragma unroll
+      for (int i = 0; i < kXyPrefetchPairs; ++i) {
+        const uint32_t t = 2 * (threadIdx.x + 256u * i);
+        if (t < TE) {
+          C2 v0 = r[2 * i], v1 = r[2 * i + 1];
+          if (P.has_phase) {
+            const uint64_t x = xy_index(P, T, t);
+            v0 = xy_phased(P, tab, table, v0, x);
+            v1 = xy_phased(P, tab, table, v1, x + 1);
+          }
+          s[t] = v0;
+          s[t + 1] = v1;
         }
       }
-      s[t] = v0;
-      s[t + 1] = v1;
+      __syncthreads();
+      if (T + gridDim.x < P.ntiles) load_regs(T + gridDim.x);
+    } else {
+      for (uint32_t t = 2 * threadIdx.x; t < TE; t += 2 * blockDim.x) {
+        const uint64_t x = xy_index(P, T, t);  // even
+        C2 v0, v1;
+        ld2(psi + x, v0, v1);
+        if (P.has_phase) {
+          v0 = xy_phased(P, tab, table, v0, x);
+          v1 = xy_phased(P, tab, table, v1, x + 1);
+        }
+        s[t] = v0;
+        s[t + 1] = v1;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     for (int g = 0; g < P.ngates; ++g) {
       const int a = P.ga[g], b = P.gb[g];
       const int lo = a < b ? a : b, hi = a < b ? b : a;
@@ -230,20 +267,20 @@ cudaError_t launch_xy_tile(const XyPass &P, bool c128, cudaStream_t s, int nsm) 
   const size_t smem = ((size_t)1 << P.tb) * (c128 ? 16 : 8) + (P.has_phase && P.ph.mode == 0 ? tabb : 0);
   static bool init = false;
   if (!init) {
-    cudaError_t e = cudaFuncSetAttribute(k_xy_tile<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_xy_tile<float2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(((size_t)1 << kXyMaxTb) * 8 + tabb));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_xy_tile<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_xy_tile<double2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(((size_t)1 << kXyMaxTb) * 16));
     if (e != cudaSuccess) return e;
     init = true;
   }
-  const uint64_t cap = (uint64_t)nsm * (c128 ? 3 : 4);  // resident CTAs per SM (shared memory)
+  const uint64_t cap = (uint64_t)nsm * 3;  // resident CTAs per SM (registers of the complex64 kernel, shared memory)
   const unsigned grid = (unsigned)(P.ntiles < cap ? P.ntiles : cap);
   if (c128)
-    k_xy_tile<double2><<<grid, 256, smem, s>>>(P);
+    k_xy_tile<double2, false><<<grid, 256, smem, s>>>(P);
   else
-    k_xy_tile<float2><<<grid, 256, smem, s>>>(P);
+    k_xy_tile<float2, true><<<grid, 256, smem, s>>>(P);
   return cudaGetLastError();
 }
 

@@ -245,6 +245,31 @@ def test_labs30_energy_vs_stored_oracle(Q, name):
     T.cuda.empty_cache()
 
 
+def test_fidelity_c64_vs_c128_labs30_p40(Q):
+    # the precision split at full size: complex64 (FP32 state, FP64 phase
+    # argument and sums) against complex128 (whose parity with the oracle is
+    # checked at n <= 24): fidelity >= 1 - 1e-6 and energy within 1e-5
+    n, p = 30, 40
+    T = torch()
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g, b = I.angles(p, 61, 0, 0.1), I.angles(p, 62)
+    s64, o64 = Q.simulate(fd, stats, g, b, state_type=Q.C64)
+    e64 = float(dev_np(o64)[0])
+    s128, o128 = Q.simulate(fd, stats, g, b, state_type=Q.C128)
+    e128 = float(dev_np(o128)[0])
+    a = s64.to(T.complex128)
+    del s64
+    ov = T.vdot(a, s128)
+    na = T.vdot(a, a).real
+    nb = T.vdot(s128, s128).real
+    fid = float((ov.abs() ** 2 / (na * nb)).item())
+    del a, s128
+    T.cuda.empty_cache()
+    assert fid > 1 - 1e-6
+    assert abs(e64 - e128) <= 1e-5 * abs(e128)
+
+
 def test_workspace_check_clean_after_runs(Q):
     n = 20
     fd = Q.labs_costs(n)
