@@ -265,17 +265,25 @@ unsigned grid_n(uint64_t work, int nsm) {
 cudaError_t launch_xy_tile(const XyPass &P, bool c128, cudaStream_t s, int nsm) {
   const size_t tabb = (size_t)kPhaseTabEntries * sizeof(float2);
   const size_t smem = ((size_t)1 << P.tb) * (c128 ? 16 : 8) + (P.has_phase && P.ph.mode == 0 ? tabb : 0);
-  static bool init = false;
-  if (!init) {
+  static int per_sm[2] = {0, 0};  // resident CTAs per SM (registers, shared memory)
+  if (!per_sm[0]) {
+    const size_t m64 = ((size_t)1 << kXyMaxTb) * 8 + tabb, m128 = ((size_t)1 << kXyMaxTb) * 16;
     cudaError_t e = cudaFuncSetAttribute(k_xy_tile<float2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(((size_t)1 << kXyMaxTb) * 8 + tabb));
+                                         (int)m64);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_xy_tile<double2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(((size_t)1 << kXyMaxTb) * 16));
+    e = cudaFuncSetAttribute(k_xy_tile<double2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m128);
     if (e != cudaSuccess) return e;
-    init = true;
+    int b64 = 0, b128 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b128, k_xy_tile<double2, false>, 256, m128) != cudaSuccess ||
+        b128 < 1)
+      b128 = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_xy_tile<float2, true>, 256, m64) != cudaSuccess ||
+        b64 < 1)
+      b64 = 1;
+    per_sm[1] = b128;
+    per_sm[0] = b64;
   }
-  const uint64_t cap = (uint64_t)nsm * 3;  // resident CTAs per SM (registers of the complex64 kernel, shared memory)
+  const uint64_t cap = (uint64_t)nsm * per_sm[c128 ? 1 : 0];
   const unsigned grid = (unsigned)(P.ntiles < cap ? P.ntiles : cap);
   if (c128)
     k_xy_tile<double2, false><<<grid, 256, smem, s>>>(P);
