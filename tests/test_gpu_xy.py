@@ -31,8 +31,8 @@ def test_dicke_state(Q, n, k, st):
 
 
 @pytest.mark.parametrize("graph", [1, 2])
-@pytest.mark.parametrize("n,st", [(4, "c64"), (9, "c128"), (12, "c64"), (13, "c64"), (16, "c64"),
-                                  (16, "c128"), (19, "c64")])
+@pytest.mark.parametrize("n,st", [(2, "c64"), (3, "c128"), (3, "c64"), (4, "c64"), (9, "c128"), (12, "c64"),
+                                  (13, "c64"), (16, "c64"), (16, "c128"), (19, "c64")])
 def test_simulate_xy_vs_oracle(Q, n, st, graph):
     stype = Q.C64 if st == "c64" else Q.C128
     f = oracle.labs_costs(n).astype(float)
