@@ -243,6 +243,17 @@ size_t qaoa_workspace_bytes(int n);
  */
 qaoa_status qaoa_workspace_check(void *d_work, size_t work_bytes, qaoa_stream_t stream);
 
+/*
+ * Diagnostic for the path above: enqueues on `stream` one kernel whose
+ * bounded device-side wait nothing completes (an mbarrier expecting bytes
+ * that no copy delivers).  It gives up after about one second and records
+ * the flag, so the next qaoa_workspace_check on this workspace returns
+ * QAOA_ERR_TIMEOUT and the context stays usable.  Asynchronous; errors:
+ * QAOA_ERR_INVALID_ARG (workspace NULL or smaller than its 512-byte header of
+ * counters), QAOA_ERR_CUDA (launch failure).
+ */
+qaoa_status qaoa_selftest_timeout(void *d_work, size_t work_bytes, qaoa_stream_t stream);
+
 /* ---------------------------------------------------- a2-a4: simulation */
 
 /*

@@ -897,6 +897,14 @@ qaoa_status qaoa_workspace_check(void *d_work, size_t work_bytes, qaoa_stream_t 
   return QAOA_OK;
 }
 
+qaoa_status qaoa_selftest_timeout(void *d_work, size_t work_bytes, qaoa_stream_t stream) {
+  if (!d_work || work_bytes < kWsPartials) return fail(QAOA_ERR_INVALID_ARG, "bad workspace");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  unsigned *err = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(d_work) + kWsCounters + 64);
+  CK(launch_wait_selftest(err, s), "wait self-test launch");
+  return QAOA_OK;
+}
+
 int qaoa_version(void) { return 100; }
 
 size_t qaoa_workspace_bytes(int n) {

@@ -151,6 +151,8 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
                           int swizzle_bytes);
 // TMA passes over 4-byte (int32 / float32) and 2-byte (uint16) cost vectors.
 cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm);
+// one bounded device-side wait that nothing completes (sets *err after ~1 s)
+cudaError_t launch_wait_selftest(unsigned *err, cudaStream_t s);
 cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm);
 cudaError_t launch_fwd_tma_u16(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm);
 cudaError_t launch_bwd_tma_u16(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm);

@@ -981,6 +981,31 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+
+namespace {
+
+// A bounded wait that nothing completes: one arrival that expects 16 bytes
+// of transactions, and no copy issued.  Every thread gives up after the
+// bounded wait; thread 0 records the flag the workspace check reads.
+__global__ void k_wait_selftest(unsigned *err) {
+  __shared__ alignas(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_expect_tx(&bar, 16u);
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0);
+  if (!ok && threadIdx.x == 0) atomicExch(err, 1u);
+}
+
+}  // namespace
+
+cudaError_t launch_wait_selftest(unsigned *err, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(err);
+  return cudaGetLastError();
+}
 #endif  // QAOA_TMA_CW == 4
 
 template <class PL, int K>

@@ -101,6 +101,7 @@ def lib():
             "qaoa_overlap": ([I, P, I, P, I, P, P, Z, P, P], I),
             "qaoa_grad": ([I, P, I, P, P, P, I, P, P, I, P, Z, P, P], I),
             "qaoa_workspace_check": ([P, Z, P], I),
+            "qaoa_selftest_timeout": ([P, Z, P], I),
             "qaoa_simulate_noalloc": ([I, P, I, P, P, P, I, P, I, I, P, P], I),
             "qaoa_server_create": ([P, P, Z, P], I),
             "qaoa_server_submit": ([P, P, P], I),
@@ -224,6 +225,12 @@ def workspace_check(work):
     """Raises QAOAError(timeout) if a kernel that used `work` gave up on a
     bounded device-side wait; synchronises the current stream."""
     _check(lib().qaoa_workspace_check(_ptr(work), work.numel(), _stream()))
+
+
+def selftest_timeout(work):
+    """Enqueues one kernel whose bounded device-side wait nothing completes:
+    the next workspace_check(work) raises QAOAError(timeout) (about 1 s)."""
+    _check(lib().qaoa_selftest_timeout(_ptr(work), work.numel(), _stream()))
 
 
 def precompute_costs(n, terms, cost_type=COST_I32, out=None):

@@ -186,3 +186,13 @@ def test_xy_validation_without_gpu(L):
     assert L.qaoa_dicke_state(10, 11, P(256), 0, None) == 1
     assert L.qaoa_dicke_state(10, -1, P(256), 0, None) == 1
     assert L.qaoa_dicke_state(10, 3, P(260), 0, None) == 1
+
+
+def test_workspace_entry_points_validate_without_gpu(L):
+    # NULL or undersized workspaces are refused before any CUDA call
+    P = C.c_void_p
+    small = 511  # below the counters and small outputs every workspace starts with
+    assert L.qaoa_workspace_check(None, 1 << 20, None) == 1
+    assert L.qaoa_workspace_check(P(256), small, None) == 1
+    assert L.qaoa_selftest_timeout(None, 1 << 20, None) == 1
+    assert L.qaoa_selftest_timeout(P(256), small, None) == 1

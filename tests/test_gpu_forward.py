@@ -291,3 +291,25 @@ def test_f64_costs_and_c64_state(Q, n):
     b = I.angles(2, 6)
     got, ref, o, E, O = run_case(Q, n, f, fd, g, b, "c64")
     assert rel_state_err(got, ref) < TOL["c64"]["state"]
+
+
+def test_bounded_wait_timeout_is_reported_and_context_survives(Q):
+    # a device-side wait that nothing completes gives up after about a second,
+    # the workspace check reports QAOA_ERR_TIMEOUT once, and the same context
+    # keeps producing correct results
+    n = 14
+    work = Q.workspace(n)
+    Q.workspace_check(work)
+    Q.selftest_timeout(work)
+    with pytest.raises(Q.QAOAError) as e:
+        Q.workspace_check(work)
+    assert e.value.status == 5  # QAOA_ERR_TIMEOUT
+    Q.workspace_check(work)  # the flag was cleared
+    f = oracle.labs_costs(n)
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g, b = I.angles(3, 5, 0, 0.2), I.angles(3, 6)
+    state, _ = Q.simulate(fd, stats, g, b, state_type=Q.C128, work=work)
+    ref = oracle.simulate(n, f.astype(float), g, b)
+    assert rel_state_err(dev_np(state), ref) < 1e-10
+    Q.workspace_check(work)
