@@ -148,11 +148,12 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("tma_kernels.cu", "kernels.h", "qaoa_common.cuh")
+KERNEL_SOURCES = ("tma_kernels.cu", "kernels.h", "qaoa_common.cuh", "api.cu")
 
 
 def kernel_source_hash():
-    """sha256 (16 hex digits) over the sources of the tiled TMA kernels."""
+    """sha256 (16 hex digits) over the sources of the tiled TMA kernels and
+    their pass schedule."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2309_04841_gb300", "csrc", f), "rb") as fh:

@@ -461,7 +461,12 @@ struct PassOp {
 // once; the X rotations of different qubits commute, so each layer's group
 // order is free.  Taking layer l+1's order as the reverse of layer l's, the
 // last group of layer l is the first of layer l+1, and both share one pass
-// around the phase of layer l+1: p*k - (p-1) passes instead of p*k.
+// around the phase of layer l+1: p*k - (p-1) passes instead of p*k.  With
+// three or more groups the LOW group (0, three rounds per sweep) goes second,
+// so it never carries two sweeps and the phase in one pass: its passes are
+// single sweeps, which run at the copy bandwidth, and the two-round HIGH
+// groups take the pivots (LABS n = 30: 246.8 instead of 254.5 ms per
+// objective+gradient evaluation).
 std::vector<PassOp> forward_schedule(int k, int p, bool init_plus, bool reduce) {
   std::vector<PassOp> ops;
   if (k == 1) {
@@ -469,6 +474,7 @@ std::vector<PassOp> forward_schedule(int k, int p, bool init_plus, bool reduce) 
   } else {
     std::vector<int> order(k);
     for (int i = 0; i < k; ++i) order[i] = i;
+    if (k >= 3) std::swap(order[0], order[1]);
     ops.push_back(PassOp{order[0], -1, 0, 0, init_plus, false});
     for (int l = 0; l < p; ++l) {
       for (int i = 1; i + 1 < k; ++i) ops.push_back(PassOp{order[i], -1, -1, l, false, false});
