@@ -282,11 +282,14 @@ std::vector<Group> plan_groups(int n, int TB, int chigh) {
 // every group whose new qubits fit the rows of a wider tile gets it (64-byte
 // cost rows made the cost load the slowest part of the phase passes).  c = 6
 // was measured slower (the 6 row qubits split unevenly over the two rounds).
-// With cmin = 3 (the adjoint), a plan with one group of 8-amplitude segments
-// (64-byte state rows, 9 new qubits) is taken where it saves a group: its
-// passes ran about 1.5x as long as 16-amplitude ones, and a second such group
-// (n = 30: rows 21..29) 2.7x, which loses against the extra group.
+// With cmin = 3 (the adjoint), a plan with groups of 8-amplitude segments
+// (64-byte state rows, 9 new qubits) is taken where it saves a group and
+// every such group's rows start at qubit kNarrowMaxH or below: 64-byte rows
+// read as fast as wider ones 32 KiB apart (h = 12) but lose about 37 % of the
+// bandwidth 4 MiB or more apart (h >= 19), where the extra group is cheaper
+// (n = 30: rows 21..29).
 constexpr int kMaxSegBits = 5;
+constexpr int kNarrowMaxH = 12;
 
 // every HIGH group whose new qubits fit the rows of a wider tile gets it
 void widen_groups(std::vector<Group> &gs, int n, int TB) {
@@ -323,8 +326,9 @@ std::vector<Group> tma_groups(int n, int TB, int cmin) {
   if (cmin <= 3) {
     std::vector<Group> g = plan_groups(n, TB, 3);
     widen_groups(g, n, TB);
-    const auto narrow = std::count_if(g.begin(), g.end(), [](const Group &G) { return G.high && G.c == 3; });
-    if (g.size() < best.size() && narrow <= 1) best = g;
+    const bool far = std::any_of(g.begin(), g.end(),
+                                 [](const Group &G) { return G.high && G.c == 3 && G.h > kNarrowMaxH; });
+    if (g.size() < best.size() && !far) best = g;
   }
   return best;
 }
