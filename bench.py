@@ -363,11 +363,7 @@ def run_ours(a, ws, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"LABS n={n} p={p} objective+gradient ({w['name']})",
-                   "n": n, "p": p, "state": "complex64", "cost": "int32",
-                   "angles": "gamma, beta ~ U[0, pi) seeds 6 / 16",
-                   "l2": f"inputs larger than L2 ({8 * N / 2**30:g} GiB state, {4 * N / 2**30:g} GiB cost vector)",
-                   "parallelism": f"replicas x{ws}"},
+        "config": workload_config(w, ws),
         "e2e": {"value": a.steps * ws / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 2 * p * 8, "d2h_bytes_per_step": (2 + 2 * p) * 8},
         "gpu_launches": launches,
@@ -492,6 +488,17 @@ def serving_bench(count=400, nmin=16, nmax=26, loads=(0.5, 0.8, 0.95), graphs_pe
 
 # ------------------------------------------------------- reference arm
 
+def workload_config(w, ws):
+    """The workload's description, the same on both arms."""
+    n, p = w["n"], w["p"]
+    N = 1 << n
+    return {"workload": f"LABS n={n} p={p} objective+gradient ({w['name']})",
+            "n": n, "p": p, "state": "complex64", "cost": "int32",
+            "angles": "gamma, beta ~ U[0, pi) seeds 6 / 16",
+            "l2": f"inputs larger than L2 ({8 * N / 2**30:g} GiB state, {4 * N / 2**30:g} GiB cost vector)",
+            "parallelism": f"replicas x{ws}"}
+
+
 def run_reference(a, ws, rank):
     """The oracle timed on the host cores: each step is one bounded sample
     (obj+grad at n = cpu_sample_n), expressed in n = 30 evals/s."""
@@ -511,8 +518,7 @@ def run_reference(a, ws, rank):
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000.0 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"LABS n={w['n']} p={w['p']} objective+gradient ({w['name']})",
-                       "n": w["n"], "p": w["p"]},
+            "config": workload_config(w, ws),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
