@@ -153,11 +153,17 @@ KERNEL_SOURCES = ("tma_kernels.cu", "kernels.h", "qaoa_common.cuh", "api.cu")
 
 def kernel_source_hash():
     """sha256 (16 hex digits) over the sources of the tiled TMA kernels and
-    their pass schedule."""
+    their pass schedule, comments and blank space left out (a comment edit
+    does not change what the counters measured)."""
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2309_04841_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2309_04841_gb300", "csrc", f), encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        src = "\n".join(line.strip() for line in src.splitlines() if line.strip())
+        h.update(src.encode())
     return h.hexdigest()[:16]
 
 

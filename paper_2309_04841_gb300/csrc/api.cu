@@ -2,11 +2,16 @@
 //
 // The planner turns one call into a short sequence of kernel launches on the
 // caller's stream:
-//   n <= 12          : single-CTA kernels with the whole state on chip;
-//   n >  12 (tiled)  : per layer one LOW pass (phase + the TB lowest qubits)
-//                      and ceil((n - TB) / (TB - 4)) HIGH passes (the other
-//                      qubits, TB - 4 at a time, 2^4-amplitude segments);
-//                      the adjoint repeats the same shapes in reverse.
+//   n <= 12        : single-CTA kernels with the whole state on chip;
+//   n >  12 (tiled): the qubits split into k groups, a LOW group (the TB
+//                    lowest qubits, one contiguous tile) and HIGH groups
+//                    (TB - c qubits each beside 2^c contiguous amplitudes,
+//                    c = 3..5); each layer passes over every group once, with
+//                    the phase in the pass that opens the layer, and the
+//                    group order reversed every layer so that the last pass
+//                    of one layer and the first of the next are one pass
+//                    (k - 1 passes per layer).  The adjoint runs the same
+//                    kind of schedule backwards on (psi, lambda).
 // Nothing here allocates device memory: scratch lives in the caller's
 // workspace, per-layer constants travel in the kernel parameter blocks.
 #include <algorithm>
