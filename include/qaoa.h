@@ -321,6 +321,11 @@ qaoa_status qaoa_probabilities(int n, void *d_state, qaoa_state_type st, void *d
 /*
  * Expectation sum_x |psi_x|^2 f_x (Sec. 3.1) of the state in d_state, written
  * to d_out[0] (device double).  Deterministic order.  Asynchronous.
+ * Precision: complex128 states are summed in double; for complex64 states
+ * |psi_x|^2 f_x is formed exactly as a pair of floats and summed with the
+ * rounding error of every add kept, runs of 32 terms then added in double,
+ * which agrees with a double evaluation of the same state to about 1e-14
+ * relative (the same holds for qaoa_overlap).
  */
 qaoa_status qaoa_expectation(int n, const void *d_state, qaoa_state_type st,
                              const void *d_costs, qaoa_cost_type ct,
