@@ -239,6 +239,10 @@ size_t qaoa_workspace_bytes(int n);
  * device-side wait (QAOA_ERR_TIMEOUT; the flag is then cleared).  Kernels
  * never trap or hang: a wait that runs out (about one second) records the
  * flag and the kernel returns, leaving its outputs incomplete.
+ * d_work = NULL with work_bytes = 0 checks the library's built-in scratch on
+ * the current device instead, the one qaoa_simulate_noalloc uses: this is how
+ * a caller of that entry point learns that one of its calls timed out (check
+ * before the next qaoa_simulate_noalloc call, which clears the flag).
  * Synchronises `stream`.
  */
 qaoa_status qaoa_workspace_check(void *d_work, size_t work_bytes, qaoa_stream_t stream);
@@ -248,9 +252,11 @@ qaoa_status qaoa_workspace_check(void *d_work, size_t work_bytes, qaoa_stream_t 
  * bounded device-side wait nothing completes (an mbarrier expecting bytes
  * that no copy delivers).  It gives up after about one second and records
  * the flag, so the next qaoa_workspace_check on this workspace returns
- * QAOA_ERR_TIMEOUT and the context stays usable.  Asynchronous; errors:
- * QAOA_ERR_INVALID_ARG (workspace NULL or smaller than its 512-byte header of
- * counters), QAOA_ERR_CUDA (launch failure).
+ * QAOA_ERR_TIMEOUT and the context stays usable.  d_work = NULL with
+ * work_bytes = 0 targets the built-in scratch of the current device, as in
+ * qaoa_workspace_check.  Asynchronous; errors: QAOA_ERR_INVALID_ARG
+ * (workspace NULL with a nonzero size, or smaller than its 512-byte header
+ * of counters), QAOA_ERR_CUDA (launch failure).
  */
 qaoa_status qaoa_selftest_timeout(void *d_work, size_t work_bytes, qaoa_stream_t stream);
 
@@ -291,12 +297,19 @@ qaoa_status qaoa_simulate(int n, const void *d_costs, qaoa_cost_type ct,
  * loads the library holds until the process exits.
  *   - Maximum n = 23; a larger n returns QAOA_ERR_OUT_OF_MEMORY with a
  *     message, before anything is enqueued.
- *   - The first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before any stream capture.
+ *   - Every call looks up that array's device address (cudaGetSymbolAddress)
+ *     with the device current.  The driver commits the array's memory when
+ *     it loads this library's device code on a device; with CUDA's lazy
+ *     module loading (the default) that can be the first call, so a caller
+ *     whose memory budget will later be full should make its first call (or
+ *     a qaoa_workspace_check(NULL, 0, stream)) while memory is still free;
+ *     make that first call before any stream capture too.
  *   - All calls share the one array and each call clears the parts that must
  *     start at zero.  Calls that overlap on the GPU (different streams,
  *     different host threads) race on it: order them on one stream.
+ *   - A bounded device-side wait that runs out sets the error word in the
+ *     built-in scratch: qaoa_workspace_check(NULL, 0, stream) reports it
+ *     (QAOA_ERR_TIMEOUT) until the next call of this entry point clears it.
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  * Arguments, results and errors otherwise as qaoa_simulate.
  */

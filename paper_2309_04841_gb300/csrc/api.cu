@@ -874,6 +874,7 @@ bool dyadic_scale(const double *w, size_t m, int *e_out) {
 
 namespace qaoa {
 void set_last_error(const char *msg) { fail(QAOA_OK, msg); }
+qaoa_status builtin_scratch(void **ptr, size_t *bytes);  // noalloc.cu
 }  // namespace qaoa
 
 // =================================================================== C ABI
@@ -899,6 +900,8 @@ const char *qaoa_status_string(qaoa_status st) {
 const char *qaoa_last_error_message(void) { return g_errmsg; }
 
 qaoa_status qaoa_workspace_check(void *d_work, size_t work_bytes, qaoa_stream_t stream) {
+  if (!d_work && work_bytes == 0 && builtin_scratch(&d_work, &work_bytes) != QAOA_OK)
+    return fail(QAOA_ERR_CUDA, "workspace check: cudaGetSymbolAddress of the built-in scratch failed");
   if (!d_work || work_bytes < kWsPartials) return fail(QAOA_ERR_INVALID_ARG, "bad workspace");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   unsigned h = 0;
@@ -913,6 +916,8 @@ qaoa_status qaoa_workspace_check(void *d_work, size_t work_bytes, qaoa_stream_t 
 }
 
 qaoa_status qaoa_selftest_timeout(void *d_work, size_t work_bytes, qaoa_stream_t stream) {
+  if (!d_work && work_bytes == 0 && builtin_scratch(&d_work, &work_bytes) != QAOA_OK)
+    return fail(QAOA_ERR_CUDA, "timeout self-test: cudaGetSymbolAddress of the built-in scratch failed");
   if (!d_work || work_bytes < kWsPartials) return fail(QAOA_ERR_INVALID_ARG, "bad workspace");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   unsigned *err = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(d_work) + kWsCounters + 64);

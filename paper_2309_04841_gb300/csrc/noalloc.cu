@@ -8,8 +8,6 @@
 // doubles; the reduction partials, counters and error word live in
 // g_scratch below, a file-scope device array that every GPU which loads this
 // library holds until the process exits.
-#include <mutex>
-
 #include "../../include/qaoa.h"
 
 namespace qaoa {
@@ -24,27 +22,29 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch for each device.  In host code the name
+// Device address of g_scratch on the current device.  In host code the name
 // g_scratch is only a host-side stand-in, not a device address, so it is
-// looked up once per device with cudaGetSymbolAddress while that device is
-// current.
-void *g_scratch_dev[kMaxDevices] = {nullptr};
-std::mutex g_mu;
-
+// looked up with cudaGetSymbolAddress while the device is current -- on every
+// call: the lookup is a cheap host-side query, and a module reloaded after a
+// device reset may place the array elsewhere.
 qaoa_status scratch_for_current_device(void **out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QAOA_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_dev[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return QAOA_ERR_CUDA;
-    g_scratch_dev[dev] = p;
-  }
-  *out = g_scratch_dev[dev];
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return QAOA_ERR_CUDA;
+  *out = p;
   return QAOA_OK;
 }
 
 }  // namespace
+
+namespace qaoa {
+// The built-in scratch of the current device, for qaoa_workspace_check and
+// qaoa_selftest_timeout called with (NULL, 0).
+qaoa_status builtin_scratch(void **ptr, size_t *bytes) {
+  const qaoa_status s = scratch_for_current_device(ptr);
+  if (s == QAOA_OK) *bytes = kScratchBytes;
+  return s;
+}
+}  // namespace qaoa
 
 extern "C" qaoa_status qaoa_simulate_noalloc(int n, const void *d_costs, qaoa_cost_type ct,
                                              const qaoa_cost_stats *stats, const double *gammas,

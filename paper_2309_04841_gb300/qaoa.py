@@ -223,14 +223,22 @@ def workspace(n, device="cuda"):
 
 def workspace_check(work):
     """Raises QAOAError(timeout) if a kernel that used `work` gave up on a
-    bounded device-side wait; synchronises the current stream."""
-    _check(lib().qaoa_workspace_check(_ptr(work), work.numel(), _stream()))
+    bounded device-side wait; synchronises the current stream.  work=None
+    checks the library's built-in scratch (the one simulate_noalloc uses)."""
+    if work is None:
+        _check(lib().qaoa_workspace_check(None, 0, _stream()))
+    else:
+        _check(lib().qaoa_workspace_check(_ptr(work), work.numel(), _stream()))
 
 
 def selftest_timeout(work):
     """Enqueues one kernel whose bounded device-side wait nothing completes:
-    the next workspace_check(work) raises QAOAError(timeout) (about 1 s)."""
-    _check(lib().qaoa_selftest_timeout(_ptr(work), work.numel(), _stream()))
+    the next workspace_check(work) raises QAOAError(timeout) (about 1 s).
+    work=None targets the built-in scratch."""
+    if work is None:
+        _check(lib().qaoa_selftest_timeout(None, 0, _stream()))
+    else:
+        _check(lib().qaoa_selftest_timeout(_ptr(work), work.numel(), _stream()))
 
 
 def precompute_costs(n, terms, cost_type=COST_I32, out=None):

@@ -60,3 +60,44 @@ def test_noalloc_rejects_n_beyond_scratch(Q):
                                        Q._stream())
     assert st == 2  # QAOA_ERR_OUT_OF_MEMORY
     assert b"n > 23" in Q.lib().qaoa_last_error_message()
+
+
+def test_noalloc_allocates_no_device_memory(Q):
+    # the entry point's promise: after a warm-up call (which may load the
+    # library's device code), a call changes the free device memory by nothing
+    import torch
+    n = 23
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    state = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    g, b = I.angles(2, 44, 0, 0.2), I.angles(2, 45)
+    Q.simulate_noalloc(fd, stats, g, b, state=state, out=out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    Q.simulate_noalloc(fd, stats, g, b, state=state, out=out)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+
+
+def test_noalloc_timeout_reported_once_through_builtin_scratch(Q):
+    # a caller of the no-allocation entry point has no workspace pointer: it
+    # checks the built-in scratch with workspace_check(None), which reports a
+    # bounded wait that ran out exactly once
+    n = 16
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g, b = I.angles(2, 46, 0, 0.2), I.angles(2, 47)
+    Q.simulate_noalloc(fd, stats, g, b)
+    Q.workspace_check(None)
+    Q.selftest_timeout(None)
+    with pytest.raises(Q.QAOAError) as e:
+        Q.workspace_check(None)
+    assert e.value.status == 5  # QAOA_ERR_TIMEOUT
+    Q.workspace_check(None)  # cleared after one report
+    _, out = Q.simulate_noalloc(fd, stats, g, b)
+    _, ref = Q.simulate(fd, stats, g, b)
+    o, r = out.cpu().numpy(), ref.cpu().numpy()
+    assert abs(o[0] - r[0]) <= 1e-5 * abs(r[0])
+    Q.workspace_check(None)
