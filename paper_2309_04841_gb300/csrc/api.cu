@@ -68,21 +68,22 @@ qaoa_status cuda_fail(cudaError_t e, const char *where) {
     if (_e != cudaSuccess) return cuda_fail(_e, "TMA pass launch"); \
   } while (0)
 
-// Profile label of a TMA pass: "fwd_high.k7" etc.  Kind bits: forward 1 =
-// first sweep, 2 = phase, 4 = second sweep, 8 = energy / overlap; adjoint (the
+// Profile label of a TMA pass: "fwd_high.k7" etc.  Group kind g: 0 LOW, 1
+// HIGH, 2 HIGH on a cluster pair ("bwd_pair").  Kind bits: forward 1 = first
+// sweep, 2 = phase, 4 = second sweep, 8 = energy / overlap; adjoint (the
 // first un-mix sweep is always there) 2 = d/d gamma + un-phase, 4 = second
 // un-mix sweep, 8 = lambda = f psi.
-const char *tma_pass_name(bool fwd, bool high, int k) {
-  static char names[2][2][16][24];
+const char *tma_pass_name(bool fwd, int g, int k) {
+  static char names[2][3][16][24];
   static std::once_flag once;
   std::call_once(once, [] {
+    static const char *gn[3] = {"low", "high", "pair"};
     for (int f = 0; f < 2; ++f)
-      for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < 3; ++h)
         for (int j = 0; j < 16; ++j)
-          snprintf(names[f][h][j], sizeof(names[f][h][j]), "%s_%s.k%d", f ? "fwd" : "bwd",
-                   h ? "high" : "low", j);
+          snprintf(names[f][h][j], sizeof(names[f][h][j]), "%s_%s.k%d", f ? "fwd" : "bwd", gn[h], j);
   });
-  return names[fwd ? 1 : 0][high ? 1 : 0][k & 15];
+  return names[fwd ? 1 : 0][g < 0 ? 0 : g > 2 ? 2 : g][k & 15];
 }
 
 int num_sms() {
@@ -259,6 +260,7 @@ struct Group {
   bool high;
   int c, h;          // geometry
   uint32_t rot;      // tile bits rotated
+  bool cl = false;   // adjoint cluster pair: also rotates the qubit h + TB - c
 };
 
 // LOW group + HIGH groups covering qubits [TB, n), TB - chigh per pass
@@ -336,6 +338,48 @@ std::vector<Group> tma_groups(int n, int TB, int cmin) {
     if (g.size() < best.size() && !far) best = g;
   }
   return best;
+}
+
+// Adjoint groups with cluster pairs: the LOW group (qubits 0..TB-1), then
+// HIGH groups of 2^c contiguous amplitudes (c = 4) times TB - c local rows,
+// of which a cluster group adds one more row qubit (h + TB - c) held by the
+// other CTA of a pair: TB - c + 1 new qubits per group instead of TB - c.
+// Taken where it needs fewer groups than the plain plan (LABS n = 30:
+// {0-11}, {12-20}, {21-29} -- three groups, two passes per layer, instead of
+// four), or as many but the plain plan needs 8-amplitude segments; only as
+// many groups as necessary are cluster pairs.
+std::vector<Group> bwd_groups(int n, int TB) {
+  std::vector<Group> plain = tma_groups(n, TB, 3);
+  const int c = 4, rows = TB - c;
+  const int R = n - TB;  // qubits above the LOW group
+  if (R <= 0) return plain;
+  const int k = (R + rows) / (rows + 1);      // HIGH groups, rows + 1 qubits at most each
+  const int ncl = R - rows * k > 0 ? R - rows * k : 0;  // groups that need the extra qubit
+  const bool narrow = std::any_of(plain.begin(), plain.end(), [](const Group &G) { return G.high && G.c == 3; });
+  if (!(1 + k < (int)plain.size() || (1 + k == (int)plain.size() && narrow && ncl > 0))) return plain;
+  std::vector<Group> gs;
+  gs.push_back(Group{false, TB, TB, (1u << TB) - 1u});
+  int q0 = TB;
+  for (int g = 0; g < k; ++g) {
+    const bool cl = g >= k - ncl;  // the top groups take the pairs
+    const int len = std::min(rows + (cl ? 1 : 0), n - q0);
+    Group G;
+    G.high = true;
+    G.c = c;
+    G.cl = cl;
+    // local rows h .. h + rows - 1 (and the pair's qubit h + rows); a group
+    // at the top of the range starts lower and rotates only its new qubits
+    const int span = rows + (cl ? 1 : 0);
+    G.h = q0 + span <= n ? q0 : n - span;
+    G.rot = 0;
+    for (int j = c; j < TB; ++j) {
+      const int q = G.h + j - c;
+      if (q >= q0 && q < q0 + len) G.rot |= 1u << j;
+    }
+    gs.push_back(G);
+    q0 += len;
+  }
+  return gs;
 }
 
 Geom make_geom(int n, const Group &G, int TB) {
@@ -745,7 +789,7 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
     const double N = (double)(1ull << n);
     const double bytes = (P.init_plus ? 8.0 : 16.0) * N + ((P.has_phase || P.reduce) ? cost_bytes(ct) * N : 0.0);
     const int kind = (op.l1 >= 0 ? 1 : 0) | (P.has_phase ? 2 : 0) | (op.l2 >= 0 ? 4 : 0) | (P.reduce ? 8 : 0);
-    LAUNCH_N(tma_pass_name(true, G.high, kind), bytes, s,
+    LAUNCH_N(tma_pass_name(true, G.high ? 1 : 0, kind), bytes, s,
              ct == QAOA_COST_U16 ? launch_fwd_tma_u16(P, G.high, s, nsm) : launch_fwd_tma(P, G.high, s, nsm));
   }
   return QAOA_OK;
@@ -760,7 +804,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
   // one group of 8-amplitude segments where that saves a group (n = 29:
   // 12 + 9 + 8 qubits in three groups instead of four); a HIGH group with
   // 8-amplitude segments rotates 9 tile bits, tile bit 3 as a lane bit
-  const std::vector<Group> gs = tma_groups(n, TB, 3);
+  const std::vector<Group> gs = bwd_groups(n, TB);
   const std::vector<PassOp> ops = adjoint_schedule((int)gs.size(), p);
   const int nsm = num_sms();
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
@@ -777,13 +821,26 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     CK(make_tile_map(&P.map_lam, lam, n, TB, h, c, 8, sw), "tensor map (lambda)");
     P.psi = reinterpret_cast<float2 *>(state);
     P.lam = reinterpret_cast<float2 *>(lam);
-    CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, (int)cost_bytes(ct), 0),
-       "tensor map (cost)");
+    if (G.cl && op.lp >= 0)
+      CK(make_pair_cost_map(&P.map_cost, const_cast<void *>(cost), n, h, (int)cost_bytes(ct)),
+         "tensor map (pair cost)");
+    else
+      CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, (int)cost_bytes(ct), 0),
+         "tensor map (cost)");
     P.ntiles = 1ull << (n - TB);
     P.h = h;
     P.c = c;
     P.cost_kind = cost_kind(ct);
-    P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
+    // A cluster pair rotates tile bits 8..11 in round 0 (layout L0), tile
+    // bits 4..7 in round 1's registers and tile bit 12 at its lane bit 4
+    // (layout L1, see k_bwd_pair); that fixed set is its sweep.
+    Sweep pair_sweep;
+    memset(&pair_sweep, 0, sizeof(pair_sweep));
+    pair_sweep.m[0] = 0xF;
+    pair_sweep.m[1] = 0xF;
+    pair_sweep.lm[1] = 0x10;
+    P.cluster = G.cl;
+    P.s1 = G.cl ? pair_sweep : G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
     {
       const TanRot R = tan_rot(bet[op.l1], true);
       P.tau1 = R.tau;
@@ -806,7 +863,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
       P.out_g = d_grad_g + op.lp;
     }
     if (op.l2 >= 0) {
-      P.s2 = G.high ? make_sweep<High>(G.rot, false) : make_sweep<Low>(G.rot, false);
+      P.s2 = G.cl ? pair_sweep : G.high ? make_sweep<High>(G.rot, false) : make_sweep<Low>(G.rot, false);
       const TanRot R = tan_rot(bet[op.l2], true);
       P.tau2 = R.tau;
       P.form2 = R.form;
@@ -817,7 +874,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
       }
       P.out_b2 = d_grad_b + op.l2;
     }
-    if ((uses_lanes(P.s1) || uses_lanes(P.s2)) && c != 3)
+    if ((uses_lanes(P.s1) || uses_lanes(P.s2)) && c != 3 && !G.cl)
       return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
     P.init_lambda = op.init;
     P.untwist = &op == &ops.back();
@@ -828,7 +885,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     const double bytes =
         (P.init_lambda ? 24.0 : 32.0) * N + ((P.has_phase || P.init_lambda) ? cost_bytes(ct) * N : 0.0);
     const int kind = (P.has_phase ? 2 : 0) | (op.l2 >= 0 ? 4 : 0) | (P.init_lambda ? 8 : 0);
-    LAUNCH_N(tma_pass_name(false, G.high, kind), bytes, s,
+    LAUNCH_N(tma_pass_name(false, G.cl ? 2 : G.high ? 1 : 0, kind), bytes, s,
              ct == QAOA_COST_U16 ? launch_bwd_tma_u16(P, G.high, s, nsm) : launch_bwd_tma(P, G.high, s, nsm));
   }
   return QAOA_OK;

@@ -140,6 +140,10 @@ struct alignas(64) TmaBwdParams {
   float wg;           // |scale|^2 weight of the d/d gamma inner product
   int has_phase, init_lambda;
   int untwist;  // last pass: psi back to the standard basis
+  // Cluster pair (HIGH group of 9 new qubits, c = 4): two CTAs hold the two
+  // halves of a 2^13-amplitude tile (k_bwd_pair); map_cost is then the
+  // pair cost map of the phase layout for passes with a phase.
+  int cluster;
   double *partials;
   unsigned *counter;
   double *out_b1, *out_g, *out_b2;
@@ -149,6 +153,9 @@ struct alignas(64) TmaBwdParams {
 
 cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, int c, int esz,
                           int swizzle_bytes);
+// Cost tile of one CTA of a pair in the phase layout: 16 contiguous elements
+// x qubits h..h+3 and h+5..h+8, qubit h+4 fixed by the box coordinate.
+cudaError_t make_pair_cost_map(CUtensorMap *map, void *base, int n, int h, int esz);
 // TMA passes over 4-byte (int32 / float32) and 2-byte (uint16) cost vectors.
 cudaError_t launch_fwd_tma(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm);
 // one bounded device-side wait that nothing completes (sets *err after ~1 s)

@@ -86,16 +86,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   return true;
 }
 
-// Tile coordinates in the 5-D tensor-map view: (0, x1, x2, 0, x4).
+// Tile coordinates in the 5-D tensor-map view: (0, x1, x2, x3, x4).
 struct TC {
   int x1, x2, x4;
+  int x3 = 0;
 };
 
 __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, TC c, uint64_t *bar) {
   asm volatile(
       "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c.x1), "r"(c.x2), "r"(0), "r"(c.x4),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c.x1), "r"(c.x2), "r"(c.x3), "r"(c.x4),
       "r"(smem_u32(bar))
       : "memory");
 }
@@ -105,6 +106,72 @@ __device__ __forceinline__ void fence_mbar_init() {
 }
 // Barrier among the CTA's 256 threads (named barrier 1).
 __device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// ---- cluster pairs (two CTAs, distributed shared memory)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+// Split cluster barrier: every thread of both CTAs arrives (release: its
+// earlier shared-memory accesses, local or remote, are ordered before) and
+// later waits (acquire).  Arrive and wait alternate in every thread.
+__device__ __forceinline__ void cl_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cl_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// The same shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+// Push-model exchange between the CTAs of a pair: st.async writes 8 bytes
+// into the partner's shared memory and counts them on the partner's
+// mbarrier (complete_tx), which the partner waits on; no fence is involved.
+__device__ __forceinline__ void st_async(uint32_t addr, float2 v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+               "f"(v.x), "f"(v.y), "r"(bar)
+               : "memory");
+}
+// Arrival on the partner's mbarrier without memory ordering: callers issue
+// it after using the values of the shared-memory loads it covers, so those
+// loads have completed.
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_cl(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for a phase that another CTA of the cluster completes (its
+// writes are visible afterwards).
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_cl(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_cl(bar, parity))
+    if (gtimer() - t0 > kWaitNs) return false;
+  return true;
+}
 
 // TMA swizzle seen at 8-byte granularity.  SWIZZLE_128B: the 16-byte chunk
 // index inside each 128-byte row is XORed with the row index mod 8;
@@ -500,13 +567,13 @@ __device__ __forceinline__ Lay layout(uint32_t tile_elems, bool two, bool cost) 
 // so the stores are coalesced.
 template <class PL, int R>
 __device__ __forceinline__ void stg_round(const float2 (&v)[PL::NREG], float2 *g, uint64_t T,
-                                          int h, int c) {
+                                          int h, int c, uint32_t thr = thr_tile<PL, R>()) {
   constexpr uint32_t RM = PL::reg(R);
   const int midbits = h - c;
   const uint32_t cm = (1u << c) - 1u;
   auto f = [&](uint32_t t) -> uint64_t { return (uint64_t)(t & cm) | ((uint64_t)(t >> c) << h); };
   const uint64_t mid = T & ((1ull << midbits) - 1ull), top = T >> midbits;
-  float2 *b = g + ((mid << c) | (top << (h + PL::TB - c))) + f(thr_tile<PL, R>());
+  float2 *b = g + ((mid << c) | (top << (h + PL::TB - c))) + f(thr);
   uint64_t u[PL::EB];  // offset of each register bit
 #pragma unroll
   for (int k = 0; k < PL::EB; ++k) u[k] = f(pdep(1u << k, RM));
@@ -543,12 +610,18 @@ static size_t smem_bytes(int tb, bool two, bool cost) {
 
 constexpr int kThreads = 256;
 
-// After a timed-out wait the loop was left early, possibly with the load of
-// tile i (issued by the previous tile's release) still in flight: wait for
-// it, again bounded, before the CTA exits.
-__device__ __forceinline__ void drain(int aborted, uint64_t *full, int i, uint64_t ntiles) {
-  if (aborted && threadIdx.x == 0 && blockIdx.x + (uint64_t)i * gridDim.x < ntiles)
-    (void)mbar_wait(full, i & 1);
+// Abort discipline of the TMA passes.  A wait that runs out sets the CTA's
+// flag; every thread reads the flag right after the tile's first barrier
+// (all flag writes of this tile happened before it, and none of the next
+// tile can happen before the tile's last barrier), so the whole CTA takes
+// the same decision, and from then on no load is issued.  The loop is left
+// at the top of the next tile; the only load that can still be in flight is
+// the one of tile i - 1 whose wait ran out (with its early cost part): wait
+// for it, again bounded, before the CTA exits.  A load still outstanding
+// after that second bounded wait would mean the copy engine stopped
+// delivering; nothing the kernel does then can make its exit safer.
+__device__ __forceinline__ void drain(int aborted, uint64_t *full, int i) {
+  if (aborted && threadIdx.x == 0 && i > 0) (void)mbar_wait(full, (i - 1) & 1);
 }
 
 // Pass kinds, fixed at compile time so each instantiation carries only its
@@ -601,8 +674,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
     if (!P.init_plus) tma_load(buf, &P.map_psi, c, full);
     if (cost) tma_load(base + L.cost_off, &P.map_cost, c, full);
   };
+  int abort_now = 0;  // uniform over the CTA: read after the tile's first barrier
+  auto read_abort = [&]() { abort_now = s_abort; };
   auto cost_next = [&](uint64_t T) {
-    if (tid == 0 && T + gridDim.x < P.ntiles) {
+    if (tid == 0 && T + gridDim.x < P.ntiles && !abort_now) {
       mbar_add_tx(full, L.cost_bytes);
       tma_load(base + L.cost_off, &P.map_cost, coords(T + gridDim.x), full);
     }
@@ -610,7 +685,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
   // after the tile's last shared-memory read: the buffers go to the next load
   auto release = [&](uint64_t T) {
     cbar();
-    if (tid == 0 && T + gridDim.x < P.ntiles) issue(T + gridDim.x, need_cost && !early_cost);
+    if (tid == 0 && T + gridDim.x < P.ntiles && !abort_now) issue(T + gridDim.x, need_cost && !early_cost);
   };
 
   if (tid == 0 && blockIdx.x < P.ntiles) issue(blockIdx.x, need_cost);
@@ -622,8 +697,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
     if (T >= P.ntiles) break;
     // A timed-out wait flags the abort and still runs this tile (on stale
     // data) through the same barriers as every other thread; all threads
-    // see the flag after those barriers and leave together.
-    if (s_abort) break;
+    // read the flag after the tile's first barrier and leave together.
+    if (abort_now) break;
     if (!mbar_wait(full, i & 1)) {
       s_abort = 1;
       atomicExch(P.err, 1u);
@@ -644,7 +719,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
     }
     if constexpr (H1) {
       rot_tw<EB>(v, P.s1.m[0], P.tau1, P.form1);
-      xp<PL, 0, 1, SW>(v, buf);
+      xp_hook<PL, 0, 1, SW>(v, buf, read_abort);
       if constexpr (NR == 2 && !H2 && !RED) release(T);
       rot_tw<EB>(v, P.s1.m[1], P.tau1, P.form1);
       if constexpr (NR == 3) {
@@ -676,9 +751,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
       if constexpr (PH) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tab, P.scl_phase);
       rot_tw<EB>(v, P.s2.m[0], P.tau2, P.form2);
       if constexpr (early_cost)
-        xp_hook<PL, 0, 1, SW>(v, buf, [&] { cost_next(T); });
+        xp_hook<PL, 0, 1, SW>(v, buf, [&] { read_abort(); cost_next(T); });
       else
-        xp<PL, 0, 1, SW>(v, buf);
+        xp_hook<PL, 0, 1, SW>(v, buf, read_abort);
       if constexpr (NR == 2 && !RED) release(T);
       rot_tw<EB>(v, P.s2.m[1], P.tau2, P.form2);
       if constexpr (NR == 3) {
@@ -707,7 +782,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
     }
     stg_round<PL, RS>(v, P.psi, T, P.h, P.c);
   }
-  drain(s_abort, full, i, P.ntiles);
+  drain(abort_now, full, i);
   if constexpr (RED) {
     double a[2] = {acc_e.value(), acc_o.value()};
     csum<2>(a, red);
@@ -727,14 +802,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_fwd_tma(const __grid_constant__
 
 // d/d gamma term Im <lambda| f |psi> of the round's amplitudes, then psi and
 // lambda times the un-phase factor exp(+i g f) (phase mode M as in phase_of).
-template <class PL, int R, int M>
+// CI maps a local tile offset to its cost-tile slot (identity except in the
+// pair layout L1, see k_bwd_pair).
+struct CostIdx {
+  __device__ __forceinline__ uint32_t operator()(uint32_t t) const { return t; }
+};
+template <class PL, int R, int M, class CI = CostIdx>
 __device__ __forceinline__ void unphase_round(float2 (&v)[PL::NREG], float2 (&w)[PL::NREG],
                                               const CostWord *cb, const TmaBwdParams &P,
-                                              const float2 *tab, float &ag) {
+                                              const float2 *tab, float &ag, CI ci = CI()) {
   const uint32_t tt = thr_tile<PL, R>();
 #pragma unroll
   for (int r = 0; r < PL::NREG; ++r) {
-    const uint32_t word = cb[tt | pdep(r, PL::reg(R))];
+    const uint32_t word = cb[ci(tt | pdep(r, PL::reg(R)))];
     const float f = cost_val(P.cost_kind, word);
     ag += P.wg * f * (w[r].x * v[r].y - w[r].y * v[r].x);
     float2 ph = phase_of<M>(P.ph, P.cost_kind, tab, word);
@@ -742,6 +822,19 @@ __device__ __forceinline__ void unphase_round(float2 (&v)[PL::NREG], float2 (&w)
     v[r] = cmulf(v[r], ph);
     w[r] = cmulf(w[r], ph);
   }
+}
+
+template <class PL, int R, class CI = CostIdx>
+__device__ __forceinline__ void unphase_any(float2 (&v)[PL::NREG], float2 (&w)[PL::NREG],
+                                            const CostWord *cb, const TmaBwdParams &P,
+                                            const float2 *tab, float &ag, CI ci = CI()) {
+  const int m = phase_m(P.ph);
+  if (m == 2)
+    unphase_round<PL, R, 2>(v, w, cb, P, tab, ag, ci);
+  else if (m == 3)
+    unphase_round<PL, R, 3>(v, w, cb, P, tab, ag, ci);
+  else
+    unphase_round<PL, R, 1>(v, w, cb, P, tab, ag, ci);
 }
 
 // SW: the state tiles' TMA swizzle, 128 for 16- to 64-amplitude segments, 64
@@ -788,8 +881,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
   };
   // Passes whose cost reads end before a later barrier (lambda = f psi in the
   // first round; the phase of a pivot) load the next tile's costs at that
-  // barrier, the vectors later.
+  // barrier, the vectors later.  No load is issued once the CTA has decided
+  // to abort (see drain).
   constexpr bool early_cost = (PH && H2 && !INIT) || (INIT && !PH);
+  int abort_now = 0;  // uniform over the CTA: read after the tile's first barrier
+  auto read_abort = [&]() { abort_now = s_abort; };
   auto issue = [&](uint64_t T, bool cost) {
     const TC c = coords(T);
     mbar_expect_tx(full, L.tile_bytes + (INIT ? 0u : L.tile_bytes) + (cost ? L.cost_bytes : 0u));
@@ -798,7 +894,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
     if (cost) tma_load(base + L.cost_off, &P.map_cost, c, full);
   };
   auto cost_next = [&](uint64_t T) {
-    if (tid == 0 && T + gridDim.x < P.ntiles) {
+    if (tid == 0 && T + gridDim.x < P.ntiles && !abort_now) {
       mbar_add_tx(full, L.cost_bytes);
       tma_load(base + L.cost_off, &P.map_cost, coords(T + gridDim.x), full);
     }
@@ -806,7 +902,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
   // after the tile's last shared-memory read: the buffers go to the next load
   auto release = [&](uint64_t T) {
     cbar();
-    if (tid == 0 && T + gridDim.x < P.ntiles) issue(T + gridDim.x, need_cost && !early_cost);
+    if (tid == 0 && T + gridDim.x < P.ntiles && !abort_now) issue(T + gridDim.x, need_cost && !early_cost);
   };
 
   if (tid == 0 && blockIdx.x < P.ntiles) issue(blockIdx.x, need_cost);
@@ -818,8 +914,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
     if (T >= P.ntiles) break;
     // A timed-out wait flags the abort and still runs this tile (on stale
     // data) through the same barriers as every other thread; all threads
-    // see the flag after those barriers and leave together.
-    if (s_abort) break;
+    // read the flag after the tile's first barrier and leave together.
+    if (abort_now) break;
     if (!mbar_wait(full, i & 1)) {
       s_abort = 1;
       atomicExch(P.err, 1u);
@@ -840,9 +936,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
     float a1 = 0.f, ag = 0.f, a2 = 0.f;
     unrot_tw<EB, LN>(v, w, P.s1.m[0], P.s1.lm[0], P.tau1, P.form1, P.w1[0], a1);
     if constexpr (INIT && early_cost)
-      xp_pair<PL, 0, 1, SW>(v, w, bv, bw, [&] { cost_next(T); });
+      xp_pair<PL, 0, 1, SW>(v, w, bv, bw, [&] { read_abort(); cost_next(T); });
     else
-      xp_pair<PL, 0, 1, SW>(v, w, bv, bw, NoHook());
+      xp_pair<PL, 0, 1, SW>(v, w, bv, bw, [&] { read_abort(); });
     if constexpr (NR == 2 && !PH && !H2) release(T);
     unrot_tw<EB, LN>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
     if constexpr (NR == 3) {
@@ -852,13 +948,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
     }
     if constexpr (PH) {
       // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
-      const int m = phase_m(P.ph);
-      if (m == 2)
-        unphase_round<PL, NR - 1, 2>(v, w, cb, P, tab, ag);
-      else if (m == 3)
-        unphase_round<PL, NR - 1, 3>(v, w, cb, P, tab, ag);
-      else
-        unphase_round<PL, NR - 1, 1>(v, w, cb, P, tab, ag);
+      unphase_any<PL, NR - 1>(v, w, cb, P, tab, ag);
       if constexpr (!H2) release(T);
     }
     if constexpr (H2) {
@@ -890,7 +980,271 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
     accg.add(ag);
     acc2.add(a2);
   }
-  drain(s_abort, full, i, P.ntiles);
+  drain(abort_now, full, i);
+  double a[3] = {acc1.value(), accg.value(), acc2.value()};
+  csum<3>(a, red);
+  if (tid == 0) {
+    P.partials[blockIdx.x * 3] = a[0];
+    P.partials[blockIdx.x * 3 + 1] = a[1];
+    P.partials[blockIdx.x * 3 + 2] = a[2];
+  }
+  double *o1 = P.out_b1, *og = P.out_g, *o2 = P.out_b2;
+  final_reduce<3>(P.partials, gridDim.x, P.counter, red, [=](double(&a)[3]) {
+    if (o1) *o1 += 2.0 * a[0];
+    if (og) *og += 2.0 * a[1];
+    if (o2) *o2 += 2.0 * a[2];
+  });
+}
+
+// ------------------------------------------------- adjoint on cluster pairs
+//
+// A HIGH group of 9 new qubits: the 2^13-amplitude tile (2^4 contiguous
+// amplitudes x 9 row qubits h..h+8, tile bits 0..12) is split over the two
+// CTAs of a cluster, each holding 2^12 amplitudes of psi and of lambda with
+// the two-round plan of the 2^12 tiles.  Two layouts of the halves:
+//   L0: CTA rank = tile bit 12, local offset = tile bits 0..11 (the halves
+//       the tensor-map loads bring in; round 0);
+//   L1: CTA rank = tile bit 8, tile bit 12 at local position 8 (round 1,
+//       where position 8 is a lane bit: that qubit is rotated by shuffles).
+// Going from one layout to the other, each CTA keeps the amplitudes whose
+// local position-8 bit equals its rank and pushes the other half (16 KB of
+// psi, 16 KB of lambda) into the partner's shared memory with st.async, at
+// the slots with that bit flipped -- exactly the slots the partner is
+// vacating; the bytes are counted on the partner's exchange mbarrier
+// (complete_tx), on which it waits.  Before pushing, a CTA waits until the
+// partner's 8 warps have signalled (a relaxed remote arrive after using the
+// values they loaded) that they have read those slots.  Sweep 1 rotates
+// round 0 (tile bits 8..11) in L0, exchanges, then round 1 (tile bits 4..7
+// and, by shuffles, tile bit 12) in L1; sweep 2 (pivots) the reverse, back
+// to L0.  The phase runs in L1, so those passes load the cost tile of the
+// L1 half (a tensor map whose box fixes tile bit 8), stored with tile bits
+// 9..12 at slots 8..11.  Single-sweep passes store from L1, pivots from L0;
+// either way each CTA writes whole 16-amplitude rows.  (A layout L1 with
+// the rank on passenger bit 3 needs one exchange per pivot instead of two,
+// but its 64-byte half rows made every pair pass slower.)
+//
+// Every wait is a bounded mbarrier wait; the cluster barrier runs only once
+// at the start (the partner's mbarriers are initialised before any remote
+// arrive) and once at the end (neither CTA leaves while the other may still
+// push into it), and both CTAs always reach it.
+struct PairCostIdx {  // local L1 offset -> slot of the L1 cost tile
+  __device__ __forceinline__ uint32_t operator()(uint32_t t) const {
+    return (t & 0xFFu) | ((t >> 1) & 0x700u) | ((t & 0x100u) << 3);
+  }
+};
+
+// One vector from round R's registers into the other layout: keep (store to
+// the own slot) where local position 8 equals RANK, else push to the
+// partner's slot with position 8 flipped.
+template <class PL, int R, uint32_t RANK>
+__device__ __forceinline__ void pair_xchg(const float2 (&v)[PL::NREG], float2 *buf, uint32_t rbuf,
+                                          uint32_t rbar) {
+  const uint32_t tt = thr_tile<PL, R>();
+#pragma unroll
+  for (int r = 0; r < PL::NREG; ++r) {
+    const uint32_t t = tt | pdep(r, PL::reg(R));
+    if (((t >> 8) & 1u) != RANK)
+      st_async(rbuf + tswz<128>(t ^ 0x100u) * 8u, v[r], rbar);
+    else
+      buf[tswz<128>(t)] = v[r];
+  }
+}
+
+template <class PL, int R>
+__device__ __forceinline__ void pair_xchg2(const float2 (&v)[PL::NREG], const float2 (&w)[PL::NREG],
+                                           float2 *bv, float2 *bw, uint32_t rbv, uint32_t rbw,
+                                           uint32_t rbar, uint32_t rank) {
+  if (rank == 0u) {
+    pair_xchg<PL, R, 0u>(v, bv, rbv, rbar);
+    pair_xchg<PL, R, 0u>(w, bw, rbw, rbar);
+  } else {
+    pair_xchg<PL, R, 1u>(v, bv, rbv, rbar);
+    pair_xchg<PL, R, 1u>(w, bw, rbw, rbar);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads, 2) k_bwd_pair(const __grid_constant__ TmaBwdParams P) {
+  using PL = PlanTmaB12High;
+  constexpr int NREG = PL::NREG, EB = PL::EB, SW = 128;
+  constexpr bool PH = (K & kPH) != 0, H2 = (K & kH2) != 0, INIT = (K & kINIT) != 0;
+  constexpr bool need_cost = PH || INIT;
+  constexpr uint32_t kXBytes = (1u << PL::TB) / 2u * 8u * 2u;  // half of psi and of lambda
+  static_assert(PL::NR == 2 && PL::lane(1) == 0x010Fu && PL::reg(0) == 0x0F00u,
+                "pair layout L1 needs local position 8 as lane bit 4 of round 1");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = aligned_base(smem_raw);
+  const Lay L = layout(1u << PL::TB, true, need_cost);
+  float2 *bv = reinterpret_cast<float2 *>(base);
+  float2 *bw = reinterpret_cast<float2 *>(base + L.lam_off);
+  const CostWord *cb = reinterpret_cast<const CostWord *>(base + L.cost_off);
+  float2 *tab = reinterpret_cast<float2 *>(base + L.tab_off);
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off);
+  double *red = reinterpret_cast<double *>(base + L.red_off);
+  __shared__ alignas(8) uint64_t xbar[4];  // free 1, exchange 1, free 2, exchange 2
+  __shared__ int s_abort;
+  const int tid = threadIdx.x;
+  const uint32_t lane = tid & 31u;
+  const int midbits = P.h - P.c;  // local tile number bit of the rank (L0)
+  const uint32_t rank = cluster_rank();
+  const uint64_t first = cluster_id(), stride = cluster_count(), nunits = P.ntiles >> 1;
+  auto tile_of = [&](uint64_t U) -> uint64_t {  // local tile number in L0
+    const uint64_t lo = U & ((1ull << midbits) - 1ull);
+    return lo | ((uint64_t)rank << midbits) | ((U >> midbits) << (midbits + 1));
+  };
+
+  if (PH && P.ph.mode == 0) fill_phase_tab<kThreads>(tab, P.ph);
+  if (tid == 0) {
+    s_abort = 0;
+    mbar_init(full, 1);
+    mbar_init(&xbar[0], 8);
+    mbar_init(&xbar[1], 1);
+    mbar_init(&xbar[2], 8);
+    mbar_init(&xbar[3], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  cl_arrive();
+  cl_wait();
+  // the partner's buffers and barriers: mapped at each use (one instruction)
+  // rather than held in registers across the tile
+  const uint32_t peer = rank ^ 1u;
+  auto remote = [&](const void *p) { return mapa(smem_u32(p), peer); };
+
+  // the state halves in L0 (the tile maps of the 2^12 tiles); the cost tile
+  // in L0 for lambda = f psi, in L1 for the phase
+  auto coords = [&](uint64_t T) {
+    TC c;
+    c.x1 = (int)(T & ((1ull << midbits) - 1ull));
+    c.x2 = 0;
+    c.x4 = (int)(T >> midbits);
+    return c;
+  };
+  auto cost_coords = [&](uint64_t U) {
+    if constexpr (INIT) return coords(tile_of(U));
+    TC c;  // [16][mid][16: tile bits 4..7][tile bit 8][tile bits 9.. and above]
+    c.x1 = (int)(U & ((1ull << midbits) - 1ull));
+    c.x2 = 0;
+    c.x3 = (int)rank;
+    c.x4 = (int)((U >> midbits) << 4);
+    return c;
+  };
+  constexpr bool early_cost = (PH && H2 && !INIT) || (INIT && !PH);
+  int abort_now = 0;
+  auto read_abort = [&]() { abort_now = s_abort; };
+  auto issue = [&](uint64_t U, bool cost) {
+    const TC c = coords(tile_of(U));
+    mbar_expect_tx(full, L.tile_bytes + (INIT ? 0u : L.tile_bytes) + (cost ? L.cost_bytes : 0u));
+    tma_load(bv, &P.map_psi, c, full);
+    if (!INIT) tma_load(bw, &P.map_lam, c, full);
+    if (cost) tma_load(base + L.cost_off, &P.map_cost, cost_coords(U), full);
+  };
+  auto cost_next = [&](uint64_t U) {
+    if (tid == 0 && U + stride < nunits && !abort_now) {
+      mbar_add_tx(full, L.cost_bytes);
+      tma_load(base + L.cost_off, &P.map_cost, cost_coords(U + stride), full);
+    }
+  };
+  auto release = [&](uint64_t U) {
+    cbar();
+    if (tid == 0 && U + stride < nunits && !abort_now) issue(U + stride, need_cost && !early_cost);
+  };
+  auto flag = [&](bool ok) {
+    if (!ok) {
+      s_abort = 1;
+      atomicExch(P.err, 1u);
+    }
+  };
+  // this warp has used what it loaded: the partner may overwrite those slots
+  auto signal = [&](uint32_t rbar) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive_remote(rbar);
+  };
+
+  if (tid == 0 && first < nunits) issue(first, need_cost);
+
+  FF acc1, accg, acc2;
+  int i = 0;
+  for (;; ++i) {
+    const uint64_t U = first + (uint64_t)i * stride;
+    if (U >= nunits) break;
+    if (abort_now) break;
+    const uint64_t T = tile_of(U);
+    const uint32_t par = (uint32_t)i & 1u;
+    flag(mbar_wait(full, par));
+    if (tid == 0) {
+      mbar_expect_tx(&xbar[1], kXBytes);
+      if constexpr (H2) mbar_expect_tx(&xbar[3], kXBytes);
+    }
+    float2 v[NREG], w[NREG];
+    lds_round<PL, 0, SW>(v, bv);
+    if constexpr (INIT) {
+      const uint32_t tt = thr_tile<PL, 0>();
+#pragma unroll
+      for (int r = 0; r < NREG; ++r) {
+        const float f = cost_val(P.cost_kind, cb[tt | pdep(r, PL::reg(0))]);
+        w[r] = f2(f * v[r].x, f * v[r].y);
+      }
+    } else {
+      lds_round<PL, 0, SW>(w, bw);
+    }
+    float a1 = 0.f, ag = 0.f, a2 = 0.f;
+    unrot_tw<EB, false>(v, w, P.s1.m[0], 0u, P.tau1, P.form1, P.w1[0], a1);
+    signal(remote(&xbar[0]));
+    // L0 -> L1
+    const bool fr1 = mbar_wait_cl(&xbar[0], par);
+    flag(fr1);
+    if (fr1) pair_xchg2<PL, 0>(v, w, bv, bw, remote(bv), remote(bw), remote(&xbar[1]), rank);
+    cbar();
+    read_abort();
+    if constexpr (INIT && early_cost) cost_next(U);
+    flag(mbar_wait_cl(&xbar[1], par));
+    lds_round<PL, 1, SW>(v, bv);
+    lds_round<PL, 1, SW>(w, bw);
+    unrot_tw<EB, true>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
+    if constexpr (H2) signal(remote(&xbar[2]));
+    if constexpr (!PH && !H2) release(U);
+    if constexpr (PH) {
+      unphase_any<PL, 1>(v, w, cb, P, tab, ag, PairCostIdx());
+      if constexpr (!H2) release(U);
+    }
+    if constexpr (H2) {
+      unrot_tw<EB, true>(v, w, P.s2.m[1], P.s2.lm[1], P.tau2, P.form2, P.w2[1], a2);
+      // L1 -> L0
+      const bool fr2 = mbar_wait_cl(&xbar[2], par);
+      flag(fr2);
+      if (fr2) pair_xchg2<PL, 1>(v, w, bv, bw, remote(bv), remote(bw), remote(&xbar[3]), rank);
+      cbar();
+      if constexpr (PH && early_cost) cost_next(U);
+      flag(mbar_wait_cl(&xbar[3], par));
+      lds_round<PL, 0, SW>(v, bv);
+      lds_round<PL, 0, SW>(w, bw);
+      release(U);
+      unrot_tw<EB, false>(v, w, P.s2.m[0], 0u, P.tau2, P.form2, P.w2[0], a2);
+      stg_round<PL, 0>(v, P.psi, T, P.h, P.c);
+      stg_round<PL, 0>(w, P.lam, T, P.h, P.c);
+    } else {
+      // store from L1: local position 8 is tile bit 12 (the rank bit of the
+      // L0 tile number), tile bit 8 is this CTA's rank
+      const uint32_t thr = thr_tile<PL, 1>();
+      const uint32_t thr1 = (thr & ~0x100u) | (rank << 8);
+      const uint64_t T1 = (T & ~(1ull << midbits)) | ((uint64_t)((thr >> 8) & 1u) << midbits);
+      if (P.untwist) {
+        // popc of the amplitude index: popc(T1) + popc(thr1) = popc(T) + popc(thr)
+        const float2 z = ipow(f2(1.f, 0.f), twist_base<PL, 1>(T));
+#pragma unroll
+        for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), popc_c(r));
+      }
+      stg_round<PL, 1>(v, P.psi, T1, P.h, P.c, thr1);
+      stg_round<PL, 1>(w, P.lam, T1, P.h, P.c, thr1);
+    }
+    acc1.add(a1);
+    accg.add(ag);
+    acc2.add(a2);
+  }
+  drain(abort_now, full, i);
+  cl_arrive();
+  cl_wait();
   double a[3] = {acc1.value(), accg.value(), acc2.value()};
   csum<3>(a, red);
   if (tid == 0) {
@@ -982,6 +1336,24 @@ cudaError_t make_tile_map(CUtensorMap *map, void *base, int n, int tb, int h, in
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// [16 elements][2^(h-4)][16: qubits h..h+3][2: qubit h+4][qubits h+5..n-1];
+// box [16, 1, 16, 1, 16] (the box's last 16 are qubits h+5..h+8).
+cudaError_t make_pair_cost_map(CUtensorMap *map, void *base, int n, int h, int esz) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if (h < 4 || n < h + 9 || (esz != 4 && esz != 2)) return cudaErrorInvalidValue;
+  const cuuint64_t e = (cuuint64_t)esz;
+  const cuuint64_t dims[5] = {16, 1ull << (h - 4), 16, 2, 1ull << (n - h - 5)};
+  const cuuint64_t strides[4] = {16 * e, (1ull << h) * e, (1ull << (h + 4)) * e, (1ull << (h + 5)) * e};
+  const cuuint32_t box[5] = {16, 1, 16, 1, 16};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  const CUtensorMapDataType dt = esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
+  const CUresult r = fn(map, dt, 5, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 namespace {
 
 // A bounded wait that nothing completes: one arrival that expects 16 bytes
@@ -1046,6 +1418,56 @@ static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int n
   return cudaGetLastError();
 }
 
+// Cluster-pair adjoint passes: clusters of two CTAs, as many as fit the GPU
+// at once (cudaOccupancyMaxActiveClusters), at most one per cluster tile.
+template <int K>
+static cudaError_t launch_bwd_pair_t(const TmaBwdParams &P, cudaStream_t s, int nsm) {
+  using PL = PlanTmaB12High;
+  const size_t smem = smem_bytes(PL::TB, true, (K & (kPH | kINIT)) != 0);
+  auto kern = k_bwd_pair<K>;
+  static int ncl = 0;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (ncl == 0) {
+    const size_t mx = smem_bytes(PL::TB, true, true);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    if (e != cudaSuccess) return e;
+    cfg.gridDim = dim3(2u * (unsigned)nsm, 1, 1);
+    cfg.dynamicSmemBytes = mx;
+    int c = 0;
+    if (cudaOccupancyMaxActiveClusters(&c, kern, &cfg) != cudaSuccess || c < 1) {
+      (void)cudaGetLastError();
+      c = nsm;
+    }
+    ncl = c;
+  }
+  uint64_t clusters = (uint64_t)ncl;
+  if (clusters > (P.ntiles >> 1)) clusters = P.ntiles >> 1;
+  cfg.gridDim = dim3((unsigned)(2 * clusters), 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  return cudaLaunchKernelEx(&cfg, kern, P);
+}
+
+static cudaError_t dispatch_bwd_pair(const TmaBwdParams &P, cudaStream_t s, int nsm) {
+  const bool h2 = (P.s2.m[0] | P.s2.m[1] | P.s2.lm[1]) != 0;
+  const int k = (P.has_phase ? kPH : 0) | (h2 ? kH2 : 0) | (P.init_lambda ? kINIT : 0);
+  switch (k) {  // the kinds the adjoint schedules produce for HIGH groups
+    case 0: return launch_bwd_pair_t<0>(P, s, nsm);
+    case kINIT: return launch_bwd_pair_t<kINIT>(P, s, nsm);
+    case kPH | kH2: return launch_bwd_pair_t<kPH | kH2>(P, s, nsm);
+    case kPH: return launch_bwd_pair_t<kPH>(P, s, nsm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <class PL>
 static cudaError_t dispatch_fwd(const TmaFwdParams &P, cudaStream_t s, int nsm) {
   const bool h1 = (P.s1.m[0] | P.s1.m[1] | P.s1.m[2]) != 0;
@@ -1092,10 +1514,20 @@ cudaError_t QAOA_TMA_FN(launch_bwd_tma)(const TmaBwdParams &P, bool high, cudaSt
   if (P.c < 3 || P.c > 6 || (P.c == 3 && !high)) return cudaErrorInvalidValue;  // 8- to 64-amplitude segments
   if (!P.psi || !P.lam || ((uintptr_t)P.psi & 15u) || ((uintptr_t)P.lam & 15u))
     return cudaErrorInvalidValue;
-  for (int r = 0; r < 3; ++r)  // lane rotations: one lane bit per round, 8-amplitude segments only
-    if ((P.c != 3 && (P.s1.lm[r] | P.s2.lm[r]) != 0) || __builtin_popcount(P.s1.lm[r]) > 1 ||
+  for (int r = 0; r < 3; ++r)  // lane rotations: one lane bit per round, 8-amplitude segments or pairs
+    if ((P.c != 3 && !P.cluster && (P.s1.lm[r] | P.s2.lm[r]) != 0) || __builtin_popcount(P.s1.lm[r]) > 1 ||
         __builtin_popcount(P.s2.lm[r]) > 1)
       return cudaErrorInvalidValue;
+  if (P.cluster) {
+    // a 9-qubit HIGH group on a pair: 16-amplitude segments, the full
+    // rotation set of the two layouts, an even number of local tiles
+    const bool s2 = (P.s2.m[0] | P.s2.m[1] | P.s2.lm[1]) != 0;
+    if (!high || P.c != 4 || P.h < 4 || P.ntiles < 2 || (P.ntiles & 1) || P.s1.m[0] != 0xF ||
+        P.s1.m[1] != 0xF || P.s1.lm[0] != 0 || P.s1.lm[1] != 0x10 || P.s1.m[2] != 0 ||
+        (s2 && (P.s2.m[0] != 0xF || P.s2.m[1] != 0xF || P.s2.lm[0] != 0 || P.s2.lm[1] != 0x10)))
+      return cudaErrorInvalidValue;
+    return dispatch_bwd_pair(P, s, nsm);
+  }
   if (P.c == 3) return dispatch_bwd<PlanTmaB12High, 64>(P, s, nsm);
   return high ? dispatch_bwd<PlanTmaB12High, 128>(P, s, nsm) : dispatch_bwd<PlanTmaB12Low, 128>(P, s, nsm);
 }

@@ -184,6 +184,16 @@ WORKLOADS = {
     "maxcut3w28_p40": dict(problem="maxcut3", n=28, p=40, graph_seed=7,
                            weighted=True, weight_seed=17, gamma_seed=8,
                            beta_seed=18, ghi=0.3, cost="f32", state="c64"),
+    # LABS n = 30 at depth 40: the precision split's state-fidelity workload
+    "labs30_p40": dict(problem="labs", n=30, p=40, gamma_seed=61,
+                       beta_seed=62, ghi=0.1, cost="i32", state="c64"),
+    # two-layer gradient workloads at the headline sizes (the oracle's stored-
+    # state gradient fits host memory at n = 28; n = 30 is checked by central
+    # differences of the oracle energy)
+    "labs28_p2": dict(problem="labs", n=28, p=2, gamma_seed=8, beta_seed=18,
+                      ghi=0.05, cost="i32", state="c64"),
+    "labs30_p2": dict(problem="labs", n=30, p=2, gamma_seed=8, beta_seed=18,
+                      ghi=0.05, cost="i32", state="c64"),
 }
 
 
@@ -199,6 +209,18 @@ def workload(name, n=None):
 def workload_angles(w):
     return (angles(w["p"], w["gamma_seed"], 0.0, w["ghi"]),
             angles(w["p"], w["beta_seed"], 0.0, math.pi))
+
+
+def sample_indices(n, count, seed):
+    """``count`` distinct basis indices in [0, 2^n), sorted (count <= 2^n / 4)."""
+    N = 1 << n
+    out = np.unique(randint(seed, count, N))
+    k = 1
+    while out.size < count:
+        more = randint(seed, count, N, offset=k * count)
+        out = np.unique(np.concatenate([out, more]))
+        k += 1
+    return out[:count]
 
 
 def workload_graph(w):

@@ -7,6 +7,9 @@ oracle itself is pinned by tests/test_oracle.py.
   python tests/golden/make_golden.py --labs-max 30
   python tests/golden/make_golden.py --configs maxcut3_n14_p2 maxcut_gnp26_p6
   python tests/golden/make_golden.py --configs labs30_p10 labs30_p10_smallgamma
+  python tests/golden/make_golden.py --state-samples labs30_p40
+  python tests/golden/make_golden.py --grad labs28_p2
+  python tests/golden/make_golden.py --fd labs30_p2
 
 labs_optima.json  : LABS minimum f and number of minimisers, n = 3..labs-max
                     (exhaustive enumeration by the oracle).
@@ -15,6 +18,10 @@ oracle_<name>.json: energy, ground-state overlap and cost-vector statistics of
                     complex128.  For float32 cost workloads the oracle
                     simulates the float32-rounded cost vector (the cost vector
                     the workload defines), widened back to float64.
+oracle_<name>_amps.npy: the oracle's amplitudes at seeded sample indices and
+                    at every minimiser (--state-samples).
+oracle_grad_<name>.json: the oracle's reverse-mode gradient (--grad).
+oracle_fd_<name>.json: central differences of the oracle energy (--fd).
 """
 import argparse
 import hashlib
@@ -133,15 +140,144 @@ def config_values(name):
     print(f"{name}: E={E:.15g} O={O:.6g} ({t2 - t1:.1f}s simulate)", flush=True)
 
 
+SAMPLE_SEED = 71  # seed of the sampled amplitude indices (inputs.sample_indices)
+
+
+def state_samples(name, count):
+    """Energy, overlap and the oracle's amplitudes at `count` seeded indices
+    plus every ground state (f == f_min) of a named workload.  The amplitudes
+    go to oracle_<name>_amps.npy (complex128, in the order of the stored
+    index list: the sampled indices, then the minimisers)."""
+    w = I.workload(name)
+    n = w["n"]
+    f64, fstore = workload_costs(w)
+    sha = hashlib.sha256(np.ascontiguousarray(fstore).tobytes()).hexdigest()
+    del fstore
+    g, b = I.workload_angles(w)
+    t1 = time.time()
+    psi = oracle.simulate(n, f64, g, b)
+    t2 = time.time()
+    E = oracle.energy(n, psi, f64)
+    O = oracle.overlap(n, psi, f64)
+    fmin = float(f64.min())
+    opt = np.flatnonzero(f64 == fmin)
+    idx = np.concatenate([I.sample_indices(n, count, SAMPLE_SEED), opt]).astype(np.int64)
+    amps = np.ascontiguousarray(psi[idx])
+    np.save(os.path.join(HERE, f"oracle_{name}_amps.npy"), amps)
+    out = {
+        "workload": name, "recipe": {k: v for k, v in w.items()},
+        "energy": E, "overlap": O, "f_min": fmin, "n_min": int(opt.size),
+        "norm": float(np.vdot(psi, psi).real),
+        "samples": {"count": int(count), "seed": SAMPLE_SEED,
+                    "generator": "inputs.sample_indices(n, count, seed)",
+                    "minimisers": [int(x) for x in opt],
+                    "amplitudes": f"oracle_{name}_amps.npy",
+                    "sampled_norm2": float(np.vdot(amps[:count], amps[:count]).real)},
+        "cost_sha256": sha,
+        "oracle_seconds_simulate": t2 - t1,
+        "source": "oracle/oracle.c (oracle_simulate, oracle_energy, oracle_overlap), "
+                  "complex128, written by make_golden.py",
+    }
+    with open(os.path.join(HERE, f"oracle_{name}.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(f"{name}: E={E:.15g} O={O:.6g} ({t2 - t1:.1f}s simulate)", flush=True)
+
+
+def grad_values(name):
+    """The oracle's stored-state reverse-mode gradient of a named workload."""
+    w = I.workload(name)
+    n = w["n"]
+    f64, fstore = workload_costs(w)
+    g, b = I.workload_angles(w)
+    t1 = time.time()
+    E, dg, db = oracle.grad(n, f64, g, b)
+    t2 = time.time()
+    out = {
+        "workload": name, "recipe": {k: v for k, v in w.items()},
+        "energy": E, "dgamma": [float(x) for x in dg], "dbeta": [float(x) for x in db],
+        "cost_sha256": hashlib.sha256(np.ascontiguousarray(fstore).tobytes()).hexdigest(),
+        "oracle_seconds": t2 - t1,
+        "source": "oracle/oracle.c (oracle_grad: reverse mode over stored forward states), "
+                  "complex128, written by make_golden.py",
+    }
+    with open(os.path.join(HERE, f"oracle_grad_{name}.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    print(f"{name}: E={E:.15g} dg={dg} db={db} ({t2 - t1:.1f}s)", flush=True)
+
+
+FD_STEPS = (1e-4, 5e-5)
+
+
+def fd_values(name):
+    """Central differences of the oracle energy in every angle, at the steps
+    FD_STEPS = (h, h/2), and their Richardson combination (4 D(h/2) - D(h)) / 3,
+    whose error is O(h^4).  Every energy is one oracle simulation (Algorithm 3,
+    complex128) of the shifted angles; the raw energies are stored too."""
+    w = I.workload(name)
+    n, p = w["n"], w["p"]
+    f64, fstore = workload_costs(w)
+    sha = hashlib.sha256(np.ascontiguousarray(fstore).tobytes()).hexdigest()
+    del fstore
+    g0, b0 = I.workload_angles(w)
+    t0 = time.time()
+
+    def energy(g, b):
+        return oracle.energy(n, oracle.simulate(n, f64, g, b), f64)
+
+    E0 = energy(g0, b0)
+    comps = []
+    for which in ("gamma", "beta"):
+        for k in range(p):
+            row = {"angle": which, "layer": k, "energies": {}}
+            D = []
+            for h in FD_STEPS:
+                ep, em = [], []
+                for sgn, lst in ((1.0, ep), (-1.0, em)):
+                    g, b = g0.copy(), b0.copy()
+                    (g if which == "gamma" else b)[k] += sgn * h
+                    lst.append(energy(g, b))
+                row["energies"][repr(h)] = [ep[0], em[0]]
+                D.append((ep[0] - em[0]) / (2.0 * h))
+                print(f"{name}: d/d{which}[{k}] h={h}: {D[-1]:.12g} "
+                      f"({time.time() - t0:.0f}s)", flush=True)
+            row["central"] = D
+            row["richardson"] = (4.0 * D[1] - D[0]) / 3.0
+            comps.append(row)
+    out = {
+        "workload": name, "recipe": {k: v for k, v in w.items()},
+        "energy": E0, "steps": list(FD_STEPS),
+        "dgamma": [r["richardson"] for r in comps if r["angle"] == "gamma"],
+        "dbeta": [r["richardson"] for r in comps if r["angle"] == "beta"],
+        "components": comps,
+        "cost_sha256": sha,
+        "oracle_seconds": time.time() - t0,
+        "source": "oracle/oracle.c (oracle_simulate, oracle_energy) at shifted angles, "
+                  "complex128, central differences + Richardson, written by make_golden.py",
+    }
+    with open(os.path.join(HERE, f"oracle_fd_{name}.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--labs-max", type=int, default=0)
     ap.add_argument("--configs", nargs="*", default=[])
+    ap.add_argument("--state-samples", nargs="*", default=[],
+                    help="workloads whose sampled amplitudes are stored")
+    ap.add_argument("--samples", type=int, default=65536)
+    ap.add_argument("--grad", nargs="*", default=[], help="oracle_grad workloads")
+    ap.add_argument("--fd", nargs="*", default=[], help="finite-difference workloads")
     a = ap.parse_args()
     if a.labs_max:
         labs_optima(a.labs_max, os.path.join(HERE, "labs_optima.json"))
     for c in a.configs:
         config_values(c)
+    for c in a.state_samples:
+        state_samples(c, a.samples)
+    for c in a.grad:
+        grad_values(c)
+    for c in a.fd:
+        fd_values(c)
 
 
 if __name__ == "__main__":
