@@ -12,12 +12,27 @@ import numpy as np
 from . import build as _build
 
 _lib = None
+_lib_omp = None
 
 
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        _lib = _load(_build.build())
+    return _lib
+
+
+def lib_omp():
+    """The OpenMP build of the same source (bit-identical results; used only
+    for the benchmark's all-core CPU timing)."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = _load(_build.build_omp())
+    return _lib_omp
+
+
+def _load(path):
+    if True:
         L = C.CDLL(path)
         P = C.c_void_p
         L.oracle_costs_terms_i64.argtypes = [C.c_int, C.c_int, P, P, P, P]
@@ -43,8 +58,7 @@ def lib():
         L.oracle_simulate_xy.argtypes = [C.c_int, P, C.c_int, P, P, P, C.c_int]
         L.oracle_dicke.argtypes = [C.c_int, C.c_int, P]
         L.oracle_grad.restype = C.c_int
-        _lib = L
-    return _lib
+        return L
 
 
 def _p(a):
@@ -189,8 +203,9 @@ def overlap(n, psi, f):
     return float(lib().oracle_overlap(n, _p(psi), _p(f)))
 
 
-def grad(n, f, gammas, betas):
-    """Returns (E, dE/dgamma[p], dE/dbeta[p]) by reverse mode with stored states."""
+def grad(n, f, gammas, betas, library=None):
+    """Returns (E, dE/dgamma[p], dE/dbeta[p]) by reverse mode with stored states.
+    `library` (default lib()) may be lib_omp() for all-core timing."""
     f = np.ascontiguousarray(f, dtype=np.float64)
     g = np.ascontiguousarray(gammas, dtype=np.float64)
     b = np.ascontiguousarray(betas, dtype=np.float64)
@@ -198,7 +213,7 @@ def grad(n, f, gammas, betas):
     e = np.zeros(1, dtype=np.float64)
     dg = np.zeros(p, dtype=np.float64)
     db = np.zeros(p, dtype=np.float64)
-    rc = lib().oracle_grad(n, _p(f), p, _p(g), _p(b), _p(e), _p(dg), _p(db))
+    rc = (library or lib()).oracle_grad(n, _p(f), p, _p(g), _p(b), _p(e), _p(dg), _p(db))
     if rc != 0:
         raise MemoryError("oracle_grad: allocation failed")
     return float(e[0]), dg, db

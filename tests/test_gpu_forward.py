@@ -237,7 +237,7 @@ def test_labs30_energy_vs_stored_oracle(Q, name):
     state, out = Q.simulate(fd, stats, g, b, state_type=Q.C64)
     o = dev_np(out)
     assert abs(o[0] - G["energy"]) <= 1e-5 * abs(G["energy"])
-    assert abs(o[1] - G["overlap"]) <= 1e-4 * G["overlap"] + 1e-12
+    assert abs(o[1] - G["overlap"]) <= 1e-5 * G["overlap"]
     T = torch()
     nrm = float(T.linalg.vector_norm(state.to(T.complex128)).item())
     assert abs(nrm - 1) < 1e-5
@@ -245,10 +245,45 @@ def test_labs30_energy_vs_stored_oracle(Q, name):
     T.cuda.empty_cache()
 
 
+def test_labs30_p40_state_vs_oracle_samples(Q):
+    # the precision split at full size against the FP64 oracle: LABS n = 30,
+    # p = 40, complex64 state.  The oracle's amplitudes are stored at 65536
+    # seeded indices and at the 16 ground states (tests/golden, written by
+    # make_golden.py --state-samples): over that sample the relative L2 error
+    # must stay below 1e-4 and the estimated infidelity below 1e-6 (the
+    # stated bound); energy and overlap within 1e-5 relative.  FP32 rounding
+    # over 40 layers of ~31 rotations and a phase predicts ~1e-6 relative per
+    # amplitude, so 1e-4 leaves two orders of margin.
+    G = _golden("labs30_p40")
+    amps_path = os.path.join(GOLDEN, G["samples"]["amplitudes"])
+    ref = np.load(amps_path)
+    w = I.workload("labs30_p40")
+    idx = np.concatenate([I.sample_indices(w["n"], G["samples"]["count"], G["samples"]["seed"]),
+                          np.asarray(G["samples"]["minimisers"], dtype=np.int64)])
+    assert idx.size == ref.size
+    T = torch()
+    fd = Q.labs_costs(w["n"])
+    stats = Q.cost_stats_compute(fd)
+    assert (stats.f_min, stats.n_min) == (G["f_min"], G["n_min"])
+    g, b = I.workload_angles(w)
+    state, out = Q.simulate(fd, stats, g, b, state_type=Q.C64)
+    o = dev_np(out)
+    got = state[T.as_tensor(idx, device="cuda")].cpu().numpy().astype(np.complex128)
+    del state, fd
+    T.cuda.empty_cache()
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    infid = 1.0 - abs(np.vdot(ref, got)) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real)
+    assert err < 1e-4, err
+    assert infid < 1e-6, infid
+    assert abs(o[0] - G["energy"]) <= 1e-5 * abs(G["energy"])
+    assert abs(o[1] - G["overlap"]) <= 1e-5 * G["overlap"]
+
+
 def test_fidelity_c64_vs_c128_labs30_p40(Q):
-    # the precision split at full size: complex64 (FP32 state, FP64 phase
-    # argument and sums) against complex128 (whose parity with the oracle is
-    # checked at n <= 24): fidelity >= 1 - 1e-6 and energy within 1e-5
+    # cross-check of the two GPU paths at full size (the oracle comparison is
+    # the test above): complex64 (FP32 state, extended-precision phase
+    # argument and sums) against complex128: fidelity >= 1 - 1e-6 and energy
+    # within 1e-5
     n, p = 30, 40
     T = torch()
     fd = Q.labs_costs(n)

@@ -6,6 +6,9 @@ Tolerance: the gradient is compared norm-wise, ||g - g_ref|| / ||g_ref||,
 because single components can vanish by symmetry.  complex64 accumulates
 FP32 rounding through 2p(n+1) passes of the forward and adjoint sweeps;
 1e-4 covers p <= 40 with margin.  complex128: 1e-9."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -15,6 +18,16 @@ from paper_2309_04841_gb300 import inputs as I
 from gpu_util import dev_np, gpu_costs, oracle_costs, torch
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not generated")
+    with open(path) as fh:
+        return json.load(fh)
 
 
 @pytest.fixture(scope="module")
@@ -44,11 +57,11 @@ def test_grad_vs_oracle_labs(Q, n, p, st, tol):
 
 @pytest.mark.parametrize("cost", ["i32", "f32"])
 @pytest.mark.parametrize("n,p", [(21, 3), (21, 1)])
-def test_grad_8_amplitude_segments_vs_oracle(Q, cost, n, p):
-    # n = 21: the adjoint's HIGH group takes qubits 12..20 in 8-amplitude
-    # segments (one group instead of two), tile bit 3 rotated across lanes;
-    # int32 and float32 cost tiles (LABS energies, scaled and perturbed for
-    # the latter)
+def test_grad_cluster_pair_vs_oracle(Q, cost, n, p):
+    # n = 21: the adjoint's HIGH group takes qubits 12..20 on a cluster pair
+    # (one group instead of two; qubit 20 split across the two CTAs, rotated
+    # after the exchange); int32 and float32 cost tiles (LABS energies, scaled
+    # and perturbed for the latter)
     f = oracle.labs_costs(n).astype(float)
     if cost == "i32":
         fd = Q.labs_costs(n)
@@ -102,6 +115,26 @@ def test_grad_uncompute_returns_plus(Q):
     assert np.max(np.abs(s - 2.0 ** (-n / 2))) < 1e-5 * 2.0 ** (-n / 2) * 10
 
 
+@pytest.mark.parametrize("n", [28, 30])
+def test_grad_uncompute_drift_fullsize(Q, n):
+    # the adjoint un-applies all p = 40 layers in place with no stored state:
+    # the state it ends on must be |+> again.  Relative L2 drift
+    # ||psi_0 - |+>|| / |||+>|| below 1e-5, the threshold beyond which
+    # checkpointed states would be needed.
+    T = torch()
+    w = I.workload("labs30_p40", n=n)
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g, b = I.workload_angles(w)
+    state = T.empty(1 << n, dtype=T.complex64, device="cuda")
+    Q.grad(fd, stats, g, b, state=state)
+    plus = 2.0 ** (-n / 2)
+    drift = float(T.linalg.vector_norm((state - plus).to(T.complex128)).item())
+    del state, fd
+    T.cuda.empty_cache()
+    assert drift < 1e-5, drift
+
+
 @pytest.mark.parametrize("name", ["labs28_p40", "maxcut3w28_p40"])
 def test_grad_fullsize_directional_fd(Q, name):
     # n = 28, p = 40, all 80 gradients in one adjoint sweep; checked by a
@@ -132,11 +165,49 @@ def test_grad_fullsize_directional_fd(Q, name):
     assert abs(np.dot(grad, v) - dd) <= 1e-4 * np.linalg.norm(grad)
 
 
+def test_grad_labs30_vs_oracle_central_differences(Q):
+    # the headline size's adjoint schedule (n = 30: groups {0-11}, {12-20},
+    # {21-29}, both HIGH groups on cluster pairs) against the FP64 oracle:
+    # central differences of the oracle energy at h = 1e-4 and 5e-5 combined
+    # by Richardson extrapolation (tests/golden, make_golden.py --fd), all
+    # four angles of p = 2; complex64 at the stated 1e-4
+    G = _golden("oracle_fd_labs30_p2.json")
+    w = I.workload("labs30_p2")
+    p = w["p"]
+    fd = Q.labs_costs(w["n"])
+    stats = Q.cost_stats_compute(fd)
+    g, b = I.workload_angles(w)
+    out = dev_np(Q.grad(fd, stats, g, b, state_type=Q.C64))
+    del fd
+    torch().cuda.empty_cache()
+    ref = np.concatenate([G["dgamma"], G["dbeta"]])
+    assert abs(out[0] - G["energy"]) <= 1e-5 * abs(G["energy"])
+    assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), ref) < 1e-4
+
+
+def test_grad_labs28_vs_oracle_reverse_mode(Q):
+    # n = 28 (the gradient workloads' size): every component against the
+    # oracle's stored-state reverse-mode gradient (make_golden.py --grad)
+    G = _golden("oracle_grad_labs28_p2.json")
+    w = I.workload("labs28_p2")
+    p = w["p"]
+    fd = Q.labs_costs(w["n"])
+    stats = Q.cost_stats_compute(fd)
+    g, b = I.workload_angles(w)
+    out = dev_np(Q.grad(fd, stats, g, b, state_type=Q.C64))
+    del fd
+    torch().cuda.empty_cache()
+    ref = np.concatenate([G["dgamma"], G["dbeta"]])
+    assert abs(out[0] - G["energy"]) <= 1e-5 * abs(G["energy"])
+    assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), ref) < 1e-4
+
+
 @pytest.mark.parametrize("n", [29, 30])
 def test_grad_c64_vs_c128_fullsize(Q, n):
-    # n = 29, 30: the complex64 adjoint runs 8-amplitude segments in one or
-    # both HIGH groups; every component against the complex128 adjoint (whose
-    # own parity with the oracle is checked at n <= 16)
+    # cross-check of the two GPU paths at n = 29, 30 (the complex64 adjoint
+    # runs one or both HIGH groups on cluster pairs there): every component
+    # against the complex128 adjoint (whose own parity with the oracle is
+    # checked at n <= 16; the oracle checks at n = 28, 30 are above)
     w = I.workload("labs30_p10", n=n)
     fd = gpu_costs(w)
     stats = Q.cost_stats_compute(fd)
