@@ -58,8 +58,9 @@ typedef enum {
 } qaoa_status;
 
 /* Cost vector element types.  QAOA_COST_U16 holds integer values 0..65535,
- * the paper's compact LABS storage (Sec. 4.4: f < 2^16 for the problems it
- * simulates); half the memory and HBM traffic of int32. */
+ * the paper's compact LABS storage (Sec. 5.2, distributed simulation:
+ * f < 2^16 for the problems it simulates); half the memory and HBM traffic
+ * of int32. */
 typedef enum {
     QAOA_COST_I32 = 0,
     QAOA_COST_F32 = 1,
@@ -150,7 +151,7 @@ qaoa_status qaoa_precompute_costs(int n, const qaoa_term *terms, size_t n_terms,
 qaoa_status qaoa_labs_costs(int n, int32_t *d_costs, qaoa_stream_t stream);
 
 /*
- * The same LABS values stored as uint16 (QAOA_COST_U16; Sec. 4.4 stores the
+ * The same LABS values stored as uint16 (QAOA_COST_U16; Sec. 5.2 stores the
  * precomputed diagonal this way, its maximum (n-1)n(2n-1)/6 being below 2^16
  * for every n <= 32 taken here).  d_costs: device, 2^n uint16, 16-byte
  * aligned.  n <= 32.  Asynchronous.

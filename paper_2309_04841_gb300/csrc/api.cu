@@ -882,8 +882,10 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     P.counter = ws.counter;
     P.err = ws.err;
     const double N = (double)(1ull << n);
-    const double bytes =
-        (P.init_lambda ? 24.0 : 32.0) * N + ((P.has_phase || P.init_lambda) ? cost_bytes(ct) * N : 0.0);
+    // psi and lambda read and written (lambda not read by the first pass, not
+    // written by the last), plus the cost vector where the pass reads it
+    const double bytes = (32.0 - (P.init_lambda ? 8.0 : 0.0) - (P.untwist ? 8.0 : 0.0)) * N +
+                         ((P.has_phase || P.init_lambda) ? cost_bytes(ct) * N : 0.0);
     const int kind = (P.has_phase ? 2 : 0) | (op.l2 >= 0 ? 4 : 0) | (P.init_lambda ? 8 : 0);
     LAUNCH_N(tma_pass_name(false, G.cl ? 2 : G.high ? 1 : 0, kind), bytes, s,
              ct == QAOA_COST_U16 ? launch_bwd_tma_u16(P, G.high, s, nsm) : launch_bwd_tma(P, G.high, s, nsm));

@@ -139,7 +139,7 @@ struct alignas(64) TmaBwdParams {
   float w1[4], w2[4]; // |scale|^2 weights of the inner products taken in each round
   float wg;           // |scale|^2 weight of the d/d gamma inner product
   int has_phase, init_lambda;
-  int untwist;  // last pass: psi back to the standard basis
+  int untwist;  // last pass: psi back to the standard basis, lambda not stored
   // Cluster pair (HIGH group of 9 new qubits, c = 4): two CTAs hold the two
   // halves of a 2^13-amplitude tile (k_bwd_pair); map_cost is then the
   // pair cost map of the phase layout for passes with a phase.

@@ -66,13 +66,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                : "memory");
 }
 
+// try_wait suspends the thread (it takes no issue slots) until the phase
+// completes or kSuspendNs pass, so a waiting warp does not spin.
+constexpr uint32_t kSuspendNs = 20000;
+
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -155,10 +159,10 @@ __device__ __forceinline__ void mbar_arrive_remote(uint32_t bar) {
 __device__ __forceinline__ bool mbar_try_cl(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -975,7 +979,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
       for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), popc_c(r));
     }
     stg_round<PL, RS>(v, P.psi, T, P.h, P.c);
-    stg_round<PL, RS>(w, P.lam, T, P.h, P.c);
+    if (!P.untwist) stg_round<PL, RS>(w, P.lam, T, P.h, P.c);  // the last pass: lambda is spent
     acc1.add(a1);
     accg.add(ag);
     acc2.add(a2);
@@ -1222,7 +1226,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_pair(const __grid_constant_
       release(U);
       unrot_tw<EB, false>(v, w, P.s2.m[0], 0u, P.tau2, P.form2, P.w2[0], a2);
       stg_round<PL, 0>(v, P.psi, T, P.h, P.c);
-      stg_round<PL, 0>(w, P.lam, T, P.h, P.c);
+      if (!P.untwist) stg_round<PL, 0>(w, P.lam, T, P.h, P.c);
     } else {
       // store from L1: local position 8 is tile bit 12 (the rank bit of the
       // L0 tile number), tile bit 8 is this CTA's rank
@@ -1236,7 +1240,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_pair(const __grid_constant_
         for (int r = 0; r < NREG; ++r) v[r] = ipow(cmulf(v[r], z), popc_c(r));
       }
       stg_round<PL, 1>(v, P.psi, T1, P.h, P.c, thr1);
-      stg_round<PL, 1>(w, P.lam, T1, P.h, P.c, thr1);
+      if (!P.untwist) stg_round<PL, 1>(w, P.lam, T1, P.h, P.c, thr1);
     }
     acc1.add(a1);
     accg.add(ag);

@@ -116,3 +116,38 @@ def test_cancel_and_timeout(Q):
     st = srv.stats()
     assert st["completed"] == 1 and st["cancelled"] == 1 and st["p99_ms"] >= st["p50_ms"] > 0
     srv.close()
+
+
+def test_admitted_requests_overlap_on_device(Q):
+    # Continuous batching is more than a queue: two admitted requests that
+    # cannot fill the GPU alone (n = 17, 18: 16 and 32 tiles per pass) run at
+    # the same time on their own streams.  Their mixed wall time (first
+    # submit to last finish) must stay well below the sum of their solo
+    # service times, and each result must equal its solo result bit for bit.
+    reqs = [dict(problem=0, n=17, gammas=I.angles(20, 71, 0, 0.1), betas=I.angles(20, 72),
+                 key=0, want_grad=True),
+            dict(problem=0, n=18, gammas=I.angles(20, 73, 0, 0.1), betas=I.angles(20, 74),
+                 key=0, want_grad=True)]
+    srv = Q.Server(2 << 30, max_inflight=4)
+    solo, solo_t = [], []
+    for r in reqs:
+        best = None
+        for _ in range(5):  # the fastest of five solo runs (the first warms caches)
+            res = srv.wait(srv.submit(**r), 20)
+            t = res["finish_s"] - res["submit_s"]
+            best = t if best is None else min(best, t)
+        solo.append(res)
+        solo_t.append(best)
+    mixed_t = None
+    for _ in range(5):
+        ts = [srv.submit(**r) for r in reqs]
+        mix = [srv.wait(t, 20) for t in ts]
+        wall = max(m["finish_s"] for m in mix) - min(m["submit_s"] for m in mix)
+        mixed_t = wall if mixed_t is None else min(mixed_t, wall)
+        for a, m in zip(solo, mix):
+            assert m["status"] == 0
+            assert a["energy"] == m["energy"] and a["overlap"] == m["overlap"]
+            np.testing.assert_array_equal(a["dgamma"], m["dgamma"])
+            np.testing.assert_array_equal(a["dbeta"], m["dbeta"])
+    srv.close()
+    assert mixed_t < 0.8 * sum(solo_t), (mixed_t, solo_t)

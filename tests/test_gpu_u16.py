@@ -1,7 +1,7 @@
 """uint16 cost vectors (QAOA_COST_U16): the paper stores the LABS diagonal as
-uint16 (Sec. 4.4).  The values are the int32 ones, so every result must be
-bit-identical to the int32 run: the kernels differ only in how they load the
-cost words.  The builder itself is checked against the oracle bit-exactly."""
+uint16 (Sec. 5.2, distributed simulation).  The values are the int32 ones, so
+every result must be bit-identical to the int32 run: the kernels differ only
+in how they load the cost words.  The builder itself is checked against the oracle bit-exactly."""
 import numpy as np
 import pytest
 
