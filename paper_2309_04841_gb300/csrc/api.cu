@@ -289,14 +289,10 @@ std::vector<Group> plan_groups(int n, int TB, int chigh) {
 // every group whose new qubits fit the rows of a wider tile gets it (64-byte
 // cost rows made the cost load the slowest part of the phase passes).  c = 6
 // was measured slower (the 6 row qubits split unevenly over the two rounds).
-// With cmin = 3 (the adjoint), a plan with groups of 8-amplitude segments
-// (64-byte state rows, 9 new qubits) is taken where it saves a group and
-// every such group's rows start at qubit kNarrowMaxH or below: 64-byte rows
-// read as fast as wider ones 32 KiB apart (h = 12) but lose about 37 % of the
-// bandwidth 4 MiB or more apart (h >= 19), where the extra group is cheaper
-// (n = 30: rows 21..29).
+// Narrower, 8-amplitude segments (64-byte rows, 9 new qubits per group) read
+// slowly when their rows are far apart; the adjoint's 9-qubit groups run on
+// cluster pairs instead (bwd_groups).
 constexpr int kMaxSegBits = 5;
-constexpr int kNarrowMaxH = 12;
 
 // every HIGH group whose new qubits fit the rows of a wider tile gets it
 void widen_groups(std::vector<Group> &gs, int n, int TB) {
@@ -323,20 +319,13 @@ void widen_groups(std::vector<Group> &gs, int n, int TB) {
   }
 }
 
-std::vector<Group> tma_groups(int n, int TB, int cmin) {
+std::vector<Group> tma_groups(int n, int TB) {
   std::vector<Group> best = plan_groups(n, TB, 4);
   for (int c = 5; c <= kMaxSegBits; ++c) {
     std::vector<Group> g = plan_groups(n, TB, c);
     if (g.size() <= best.size()) best = g;
   }
   widen_groups(best, n, TB);
-  if (cmin <= 3) {
-    std::vector<Group> g = plan_groups(n, TB, 3);
-    widen_groups(g, n, TB);
-    const bool far = std::any_of(g.begin(), g.end(),
-                                 [](const Group &G) { return G.high && G.c == 3 && G.h > kNarrowMaxH; });
-    if (g.size() < best.size() && !far) best = g;
-  }
   return best;
 }
 
@@ -346,17 +335,18 @@ std::vector<Group> tma_groups(int n, int TB, int cmin) {
 // other CTA of a pair: TB - c + 1 new qubits per group instead of TB - c.
 // Taken where it needs fewer groups than the plain plan (LABS n = 30:
 // {0-11}, {12-20}, {21-29} -- three groups, two passes per layer, instead of
-// four), or as many but the plain plan needs 8-amplitude segments; only as
-// many groups as necessary are cluster pairs.
+// four; also n = 21, 29); only as many groups as necessary are cluster pairs.
+// (At n = 21 and 29 a plain plan with one 8-amplitude group has as few
+// groups; measured at n = 29: 114.1 ms per LABS p = 10 evaluation against
+// 108.8 ms with the pair.)
 std::vector<Group> bwd_groups(int n, int TB) {
-  std::vector<Group> plain = tma_groups(n, TB, 3);
+  std::vector<Group> plain = tma_groups(n, TB);
   const int c = 4, rows = TB - c;
   const int R = n - TB;  // qubits above the LOW group
   if (R <= 0) return plain;
   const int k = (R + rows) / (rows + 1);      // HIGH groups, rows + 1 qubits at most each
   const int ncl = R - rows * k > 0 ? R - rows * k : 0;  // groups that need the extra qubit
-  const bool narrow = std::any_of(plain.begin(), plain.end(), [](const Group &G) { return G.high && G.c == 3; });
-  if (!(1 + k < (int)plain.size() || (1 + k == (int)plain.size() && narrow && ncl > 0))) return plain;
+  if (!(1 + k < (int)plain.size())) return plain;
   std::vector<Group> gs;
   gs.push_back(Group{false, TB, TB, (1u << TB) - 1u});
   int q0 = TB;
@@ -727,7 +717,7 @@ qaoa_status tma_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_c
   using Low = PlanTmaF13Low;
   using High = PlanTmaF13High;
   const int TB = Low::TB;
-  const std::vector<Group> gs = tma_groups(n, TB, 4);
+  const std::vector<Group> gs = tma_groups(n, TB);
   const std::vector<PassOp> ops = forward_schedule((int)gs.size(), p, init_plus != 0, d_out != nullptr);
   const int nsm = num_sms();
   if (d_out) CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
@@ -801,9 +791,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
   using Low = PlanTmaB12Low;
   using High = PlanTmaB12High;
   const int TB = Low::TB;
-  // one group of 8-amplitude segments where that saves a group (n = 29:
-  // 12 + 9 + 8 qubits in three groups instead of four); a HIGH group with
-  // 8-amplitude segments rotates 9 tile bits, tile bit 3 as a lane bit
+  // HIGH groups of 9 new qubits on cluster pairs where they save a group
   const std::vector<Group> gs = bwd_groups(n, TB);
   const std::vector<PassOp> ops = adjoint_schedule((int)gs.size(), p);
   const int nsm = num_sms();
@@ -816,9 +804,8 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
     const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
-    const int sw = c == 3 ? 64 : 128;  // a 128-byte swizzle pads 64-byte box rows
-    CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, sw), "tensor map (psi)");
-    CK(make_tile_map(&P.map_lam, lam, n, TB, h, c, 8, sw), "tensor map (lambda)");
+    CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, 128), "tensor map (psi)");
+    CK(make_tile_map(&P.map_lam, lam, n, TB, h, c, 8, 128), "tensor map (lambda)");
     P.psi = reinterpret_cast<float2 *>(state);
     P.lam = reinterpret_cast<float2 *>(lam);
     if (G.cl && op.lp >= 0)
@@ -874,7 +861,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
       }
       P.out_b2 = d_grad_b + op.l2;
     }
-    if ((uses_lanes(P.s1) || uses_lanes(P.s2)) && c != 3 && !G.cl)
+    if ((uses_lanes(P.s1) || uses_lanes(P.s2)) && !G.cl)
       return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
     P.init_lambda = op.init;
     P.untwist = &op == &ops.back();

@@ -841,14 +841,10 @@ __device__ __forceinline__ void unphase_any(float2 (&v)[PL::NREG], float2 (&w)[P
     unphase_round<PL, R, 1>(v, w, cb, P, tab, ag, ci);
 }
 
-// SW: the state tiles' TMA swizzle, 128 for 16- to 64-amplitude segments, 64
-// for 8-amplitude ones (whose 64-byte box rows a 128-byte swizzle would pad
-// to 128 bytes in shared memory); the latter rotate tile bit 3, a lane bit in
-// both rounds of the two-round plan, by shuffles.
-template <class PL, int K, int SW>
+// The state tiles use the TMA 128-byte swizzle (16- to 64-amplitude segments).
+template <class PL, int K>
 __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
-  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB;
-  constexpr bool LN = SW == 64;
+  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, SW = 128;
   constexpr bool PH = (K & kPH) != 0, H2 = (K & kH2) != 0, INIT = (K & kINIT) != 0;
   constexpr bool need_cost = PH || INIT;
   constexpr int RS = H2 ? 0 : NR - 1;  // the round the tiles are stored from
@@ -938,17 +934,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
       lds_round<PL, 0, SW>(w, bw);
     }
     float a1 = 0.f, ag = 0.f, a2 = 0.f;
-    unrot_tw<EB, LN>(v, w, P.s1.m[0], P.s1.lm[0], P.tau1, P.form1, P.w1[0], a1);
+    unrot_tw<EB, false>(v, w, P.s1.m[0], P.s1.lm[0], P.tau1, P.form1, P.w1[0], a1);
     if constexpr (INIT && early_cost)
       xp_pair<PL, 0, 1, SW>(v, w, bv, bw, [&] { read_abort(); cost_next(T); });
     else
       xp_pair<PL, 0, 1, SW>(v, w, bv, bw, [&] { read_abort(); });
     if constexpr (NR == 2 && !PH && !H2) release(T);
-    unrot_tw<EB, LN>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
+    unrot_tw<EB, false>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
     if constexpr (NR == 3) {
       xp_pair<PL, 1, 2, SW>(v, w, bv, bw, NoHook());
       if constexpr (!PH && !H2) release(T);
-      unrot_tw<EB, LN>(v, w, P.s1.m[2], P.s1.lm[2], P.tau1, P.form1, P.w1[2], a1);
+      unrot_tw<EB, false>(v, w, P.s1.m[2], P.s1.lm[2], P.tau1, P.form1, P.w1[2], a1);
     }
     if constexpr (PH) {
       // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
@@ -956,13 +952,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
       if constexpr (!H2) release(T);
     }
     if constexpr (H2) {
-      unrot_tw<EB, LN>(v, w, P.s2.m[NR - 1], P.s2.lm[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
+      unrot_tw<EB, false>(v, w, P.s2.m[NR - 1], P.s2.lm[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
       if constexpr (NR == 3) {
         if constexpr (PH && early_cost)
           xp_pair<PL, 2, 1, SW>(v, w, bv, bw, [&] { cost_next(T); });
         else
           xp_pair<PL, 2, 1, SW>(v, w, bv, bw, NoHook());
-        unrot_tw<EB, LN>(v, w, P.s2.m[1], P.s2.lm[1], P.tau2, P.form2, P.w2[1], a2);
+        unrot_tw<EB, false>(v, w, P.s2.m[1], P.s2.lm[1], P.tau2, P.form2, P.w2[1], a2);
         xp_pair<PL, 1, 0, SW>(v, w, bv, bw, NoHook());
       } else if constexpr (PH && early_cost) {
         xp_pair<PL, 1, 0, SW>(v, w, bv, bw, [&] { cost_next(T); });
@@ -970,7 +966,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
         xp_pair<PL, 1, 0, SW>(v, w, bv, bw, NoHook());
       }
       release(T);
-      unrot_tw<EB, LN>(v, w, P.s2.m[0], P.s2.lm[0], P.tau2, P.form2, P.w2[0], a2);
+      unrot_tw<EB, false>(v, w, P.s2.m[0], P.s2.lm[0], P.tau2, P.form2, P.w2[0], a2);
     }
     if (P.untwist) {
       // psi back to the standard basis (lambda is scratch from here on)
@@ -1403,10 +1399,10 @@ static cudaError_t launch_fwd_tma_t(const TmaFwdParams &P, cudaStream_t s, int n
   return cudaGetLastError();
 }
 
-template <class PL, int K, int SW>
+template <class PL, int K>
 static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int nsm) {
   const size_t smem = smem_bytes(PL::TB, true, (K & (kPH | kINIT)) != 0);
-  auto kern = k_bwd_tma<PL, K, SW>;
+  auto kern = k_bwd_tma<PL, K>;
   static int nb = 0;
   if (nb == 0) {
     const size_t mx = smem_bytes(PL::TB, true, true);
@@ -1488,16 +1484,16 @@ static cudaError_t dispatch_fwd(const TmaFwdParams &P, cudaStream_t s, int nsm) 
   }
 }
 
-template <class PL, int SW>
+template <class PL>
 static cudaError_t dispatch_bwd(const TmaBwdParams &P, cudaStream_t s, int nsm) {
   const bool h2 = (P.s2.m[0] | P.s2.m[1] | P.s2.m[2] | P.s2.lm[0] | P.s2.lm[1] | P.s2.lm[2]) != 0;
   const int k = (P.has_phase ? kPH : 0) | (h2 ? kH2 : 0) | (P.init_lambda ? kINIT : 0);
   switch (k) {  // the kinds the adjoint schedules produce
-    case 0: return launch_bwd_tma_t<PL, 0, SW>(P, s, nsm);
-    case kINIT: return launch_bwd_tma_t<PL, kINIT, SW>(P, s, nsm);
-    case kPH | kH2: return launch_bwd_tma_t<PL, kPH | kH2, SW>(P, s, nsm);
-    case kPH: return launch_bwd_tma_t<PL, kPH, SW>(P, s, nsm);
-    case kPH | kINIT: return launch_bwd_tma_t<PL, kPH | kINIT, SW>(P, s, nsm);
+    case 0: return launch_bwd_tma_t<PL, 0>(P, s, nsm);
+    case kINIT: return launch_bwd_tma_t<PL, kINIT>(P, s, nsm);
+    case kPH | kH2: return launch_bwd_tma_t<PL, kPH | kH2>(P, s, nsm);
+    case kPH: return launch_bwd_tma_t<PL, kPH>(P, s, nsm);
+    case kPH | kINIT: return launch_bwd_tma_t<PL, kPH | kINIT>(P, s, nsm);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1515,11 +1511,11 @@ cudaError_t QAOA_TMA_FN(launch_fwd_tma)(const TmaFwdParams &P, bool high, cudaSt
 }
 
 cudaError_t QAOA_TMA_FN(launch_bwd_tma)(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {
-  if (P.c < 3 || P.c > 6 || (P.c == 3 && !high)) return cudaErrorInvalidValue;  // 8- to 64-amplitude segments
+  if (P.c < 4 || P.c > 6) return cudaErrorInvalidValue;  // 16- to 64-amplitude segments
   if (!P.psi || !P.lam || ((uintptr_t)P.psi & 15u) || ((uintptr_t)P.lam & 15u))
     return cudaErrorInvalidValue;
-  for (int r = 0; r < 3; ++r)  // lane rotations: one lane bit per round, 8-amplitude segments or pairs
-    if ((P.c != 3 && !P.cluster && (P.s1.lm[r] | P.s2.lm[r]) != 0) || __builtin_popcount(P.s1.lm[r]) > 1 ||
+  for (int r = 0; r < 3; ++r)  // lane rotations: cluster pairs only, one lane bit per round
+    if ((!P.cluster && (P.s1.lm[r] | P.s2.lm[r]) != 0) || __builtin_popcount(P.s1.lm[r]) > 1 ||
         __builtin_popcount(P.s2.lm[r]) > 1)
       return cudaErrorInvalidValue;
   if (P.cluster) {
@@ -1532,8 +1528,7 @@ cudaError_t QAOA_TMA_FN(launch_bwd_tma)(const TmaBwdParams &P, bool high, cudaSt
       return cudaErrorInvalidValue;
     return dispatch_bwd_pair(P, s, nsm);
   }
-  if (P.c == 3) return dispatch_bwd<PlanTmaB12High, 64>(P, s, nsm);
-  return high ? dispatch_bwd<PlanTmaB12High, 128>(P, s, nsm) : dispatch_bwd<PlanTmaB12Low, 128>(P, s, nsm);
+  return high ? dispatch_bwd<PlanTmaB12High>(P, s, nsm) : dispatch_bwd<PlanTmaB12Low>(P, s, nsm);
 }
 
 }  // namespace qaoa
