@@ -1278,6 +1278,95 @@ std::vector<XyOp> xy_schedule(int n, const std::vector<std::pair<int, int>> &edg
   return ops;
 }
 
+// The pair rotation by beta as three shears: beta reduced to [-pi/2, pi/2]
+// (a rotation by pi is the exact factor -1).
+void xy_beta(double beta, double &tb2, double &sb, int &neg) {
+  double br = std::remainder(beta, kTwoPi);  // (-pi, pi]
+  neg = 0;
+  if (br > kTwoPi / 4) {
+    br -= kTwoPi / 2;
+    neg = 1;
+  } else if (br < -kTwoPi / 4) {
+    br += kTwoPi / 2;
+    neg = 1;
+  }
+  tb2 = std::tan(br / 2);
+  sb = std::sin(br);
+}
+
+// One pass of the TMA ring schedule (XyTmaParams).
+struct XyTmaOp {
+  bool low;
+  int h;
+  uint32_t em[3];
+  int wrap;
+};
+
+// The ring's chain of gates (0,1), (1,2), ..., (n-2, n-1), (n-1, 0) over
+// passes of 2^13-amplitude tiles: the LOW pass (qubits 0..12, tile bit =
+// qubit) takes (0,1)..(11,12) in rounds over tile bits 0-4, 4-8, 8-12; each
+// HIGH pass (16 contiguous amplitudes x rows h..h+8 at tile bits 4..12) the
+// next up to 8 gates in rounds over tile bits 4-8, 8-12; the last pass ends
+// with (n-1, 0) (tile bits 12, 0).  LABS n = 28: 3 passes per layer.
+std::vector<XyTmaOp> xy_ring_tma_schedule(int n) {
+  std::vector<XyTmaOp> ops;
+  ops.push_back(XyTmaOp{true, 4, {0xF, 0xF, 0xF}, 0});
+  for (int q = 12; q <= n - 2;) {
+    const int h = q < n - 9 ? q : n - 9;
+    const int last = std::min(h + 7, n - 2);
+    XyTmaOp o{false, h, {0, 0, 0}, 0};
+    for (int qq = q; qq <= last; ++qq) {
+      const int a = qq - h + 4;  // the gate's tile bits (a, a + 1), 4 <= a <= 11
+      if (a + 1 <= 8)
+        o.em[0] |= 1u << (a - 4);
+      else
+        o.em[1] |= 1u << (a - 8);
+    }
+    ops.push_back(o);
+    q = last + 1;
+  }
+  ops.back().wrap = 1;
+  return ops;
+}
+
+qaoa_status xy_ring_tma(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                        const double *gammas, const double *betas, int p, void *state, const Ws &ws,
+                        cudaStream_t s) {
+  const std::vector<XyTmaOp> ops = xy_ring_tma_schedule(n);
+  const int nsm = num_sms();
+  const double N = (double)(1ull << n);
+  static XyTmaParams P;
+  static std::mutex *mu = new std::mutex();
+  std::lock_guard<std::mutex> lock(*mu);
+  for (int l = 0; l < p; ++l) {
+    double tb2, sb;
+    int neg;
+    xy_beta(betas[l], tb2, sb, neg);
+    for (const XyTmaOp &o : ops) {
+      memset(&P, 0, sizeof(P));
+      CK(make_tile_map(&P.map_psi, state, n, 13, o.h, 4, 8, 128), "tensor map (XY state)");
+      CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, 13, o.h, 4, (int)cost_bytes(ct), 0),
+         "tensor map (XY cost)");
+      P.psi = reinterpret_cast<float2 *>(state);
+      P.ntiles = 1ull << (n - 13);
+      P.h = o.h;
+      P.c = 4;
+      P.cost_kind = cost_kind(ct);
+      P.has_phase = o.low;  // the layer's phase opens its first pass
+      if (P.has_phase) make_phase(P.ph, gammas[l], ct, stats, 1.0);
+      for (int r = 0; r < 3; ++r) P.em[r] = o.em[r];
+      P.wrap = o.wrap;
+      P.t = (float)tb2;
+      P.s = (float)sb;
+      P.neg = neg;
+      P.err = ws.err;
+      LAUNCH("xy_tile", 16.0 * N + (P.has_phase ? cost_bytes(ct) * N : 0.0), s,
+             ct == QAOA_COST_U16 ? launch_xy_tma_u16(P, o.low, s, nsm) : launch_xy_tma(P, o.low, s, nsm));
+    }
+  }
+  return QAOA_OK;
+}
+
 qaoa_status qaoa_simulate_xy(int n, const void *d_costs, qaoa_cost_type ct, const qaoa_cost_stats *stats,
                              const double *gammas, const double *betas, int p, int graph, void *d_state,
                              qaoa_state_type st, void *d_work, size_t work_bytes, double *d_out,
@@ -1296,6 +1385,18 @@ qaoa_status qaoa_simulate_xy(int n, const void *d_costs, qaoa_cost_type ct, cons
   const bool c128 = st == QAOA_C128;
   const int nsm = num_sms();
   const double N = (double)(1ull << n), es = c128 ? 16.0 : 8.0;
+  if (!c128 && graph == QAOA_XY_RING && n >= 13 && tma_ok(ct)) {
+    // complex64 ring: register rounds on TMA-streamed tiles
+    r = xy_ring_tma(n, d_costs, ct, stats, gammas, betas, p, d_state, ws, s);
+    if (r != QAOA_OK) return r;
+    if (d_out) {
+      CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
+      LAUNCH("expect", (es + cost_bytes(ct)) * N, s,
+             launch_expect(n, d_state, c128, d_costs, cost_kind(ct), stats->f_min, ws.partials,
+                           ws.counter, d_out, 2, s, nsm));
+    }
+    return QAOA_OK;
+  }
   std::vector<XyOp> ops = xy_schedule(n, xy_edges(n, graph));
   if (ops.empty() || !ops.front().tile) {  // the phase rides on a tile pass
     XyOp o;
@@ -1311,16 +1412,9 @@ qaoa_status qaoa_simulate_xy(int n, const void *d_costs, qaoa_cost_type ct, cons
   for (int l = 0; l < p; ++l) {
     // the pair rotation by beta as three shears: beta reduced to [-pi/2, pi/2]
     // (a rotation by pi is the exact factor -1)
-    double br = std::remainder(betas[l], kTwoPi);  // (-pi, pi]
-    int neg = 0;
-    if (br > kTwoPi / 4) {
-      br -= kTwoPi / 2;
-      neg = 1;
-    } else if (br < -kTwoPi / 4) {
-      br += kTwoPi / 2;
-      neg = 1;
-    }
-    const double tb2 = std::tan(br / 2), sb = std::sin(br);
+    double tb2, sb;
+    int neg;
+    xy_beta(betas[l], tb2, sb, neg);
     const double g2 = gammas[l] / kTwoPi;
     for (size_t k = 0; k < ops.size(); ++k) {
       const XyOp &o = ops[k];

@@ -164,6 +164,39 @@ cudaError_t launch_bwd_tma(const TmaBwdParams &P, bool high, cudaStream_t s, int
 cudaError_t launch_fwd_tma_u16(const TmaFwdParams &P, bool high, cudaStream_t s, int nsm);
 cudaError_t launch_bwd_tma_u16(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm);
 
+// ---- XY ring mixer passes streamed by TMA (complex64).  A ring layer is the
+// ordered chain of gates (q, q + 1), then (n - 1, 0).  Tiles of 2^13
+// amplitudes; a round holds 5 consecutive tile bits in registers and applies
+// the chain's gates among them in order, consecutive rounds sharing one bit:
+//   LOW pass (qubits 0..12):  rounds over tile bits 0-4, 4-8, 8-12;
+//   HIGH pass (16 contiguous amplitudes x rows h..h+8 at tile bits 4..12):
+//                             rounds over tile bits 4-8, 8-12.
+// em[r] bit i: apply the gate on the round's register bits (i, i + 1).  wrap:
+// after the last round, the gate (tile bit 12, tile bit 0) = (n - 1, 0), tile
+// bit 0 being lane bit 0 there (a shuffle).
+using PlanXyLow = Plan<13, 5, 256, 0, 3, 0x001F, 0x03E0, 0x1C00, 0x01F0, 0x020F, 0x1C00,
+                       0x1F00, 0x001F, 0x00E0>;
+using PlanXyHigh = Plan<13, 5, 256, 0, 2, 0x01F0, 0x020F, 0x1C00, 0x1F00, 0x001F, 0x00E0>;
+static_assert(PlanXyLow::valid_round(0) && PlanXyLow::valid_round(1) && PlanXyLow::valid_round(2) &&
+                  PlanXyHigh::valid_round(0) && PlanXyHigh::valid_round(1),
+              "bad XY plans");
+
+struct alignas(64) XyTmaParams {
+  CUtensorMap map_psi, map_cost;
+  float2 *psi;
+  uint64_t ntiles;
+  int h, c, cost_kind;
+  int has_phase;       // the layer's phase before the gates (LOW pass)
+  uint32_t em[3];      // gate masks per round
+  int wrap;            // the gate (n - 1, 0) after the last round
+  float t, s;          // tan(b/2), sin(b) of the layer's beta reduced to |b| <= pi/2
+  int neg;             // the reduction took out a factor -1
+  unsigned *err;
+  PhaseDigits ph;
+};
+cudaError_t launch_xy_tma(const XyTmaParams &P, bool low, cudaStream_t s, int nsm);
+cudaError_t launch_xy_tma_u16(const XyTmaParams &P, bool low, cudaStream_t s, int nsm);
+
 // One XY-mixer pass over tiles of 2^tb amplitudes: qubits 0..c-1 (contiguous)
 // and h..h+tb-c-1; the gates act on tile bits (ga[g], gb[g]) in order.
 constexpr int kXyMaxTb = 12;

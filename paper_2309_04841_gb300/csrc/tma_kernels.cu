@@ -1243,6 +1243,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_pair(const __grid_constant_
     acc2.add(a2);
   }
   drain(abort_now, full, i);
+  // Every push the partner makes into this CTA's shared memory is counted on
+  // the exchange barriers and waited for within its tile; only a wait that
+  // ran out can leave one in flight (the flag is settled: the last tile's
+  // last barrier follows every flag write).  Wait for the last tile's
+  // exchange phases once more, bounded, so that no remote store is likely to
+  // land after this CTA has exited; a partner stalled beyond that means the
+  // GPU itself has stopped making progress.
+  if (s_abort && i > 0) {
+    (void)mbar_wait_cl(&xbar[1], (uint32_t)(i - 1) & 1u);
+    if constexpr (H2) (void)mbar_wait_cl(&xbar[3], (uint32_t)(i - 1) & 1u);
+  }
   cl_arrive();
   cl_wait();
   double a[3] = {acc1.value(), accg.value(), acc2.value()};
@@ -1258,6 +1269,154 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_pair(const __grid_constant_
     if (og) *og += 2.0 * a[1];
     if (o2) *o2 += 2.0 * a[2];
   });
+}
+
+// ------------------------------------------------------ XY ring mixer passes
+//
+// The XY gate exp(-i b (X_a X_b + Y_a Y_b) / 2) rotates each pair (u, w) of
+// amplitudes whose bits (a, b) are (1, 0) and (0, 1) by
+// [[cos b, -i sin b], [-i sin b, cos b]] and leaves the others alone.  As in
+// the shared-memory XY kernels it is applied as three shears of the real
+// rotation of (u, i w) (t = tan(b/2), s = sin b, b reduced to |b| <= pi/2,
+// an exact factor -1 for the rest): every shear has determinant 1, so the
+// rounding of t and s cannot make the norm drift over many gates.
+__device__ __forceinline__ void xy_gate2(float2 &u, float2 &w, float t, float s, bool neg) {
+  const float2 v = f2(-w.y, w.x);  // i w
+  const float2 x1 = f2(fmaf(-t, v.x, u.x), fmaf(-t, v.y, u.y));
+  float2 y1 = f2(fmaf(s, x1.x, v.x), fmaf(s, x1.y, v.y));
+  float2 x2 = f2(fmaf(-t, y1.x, x1.x), fmaf(-t, y1.y, x1.y));
+  if (neg) {
+    x2 = f2(-x2.x, -x2.y);
+    y1 = f2(-y1.x, -y1.y);
+  }
+  u = x2;
+  w = f2(y1.y, -y1.x);  // -i v
+}
+
+// The ring gates of one round: for each set bit i of em, the gate on the
+// round's register bits (i, i + 1) -- tile bits p + i, p + i + 1 of a round
+// whose registers are the 5 consecutive tile bits p.. -- in ascending i, the
+// order of the chain.
+template <int EB>
+__device__ __forceinline__ void xy_round(float2 (&v)[1 << EB], uint32_t em, float t, float s, bool neg) {
+#pragma unroll
+  for (int i = 0; i + 1 < EB; ++i)
+    if ((em >> i) & 1u) {
+#pragma unroll
+      for (int r = 0; r < (1 << EB); ++r)
+        if (((r >> i) & 1) && !((r >> (i + 1)) & 1)) xy_gate2(v[r], v[r ^ (3 << i)], t, s, neg);
+    }
+}
+
+// The gate (tile bit 12, tile bit 0) after the last round of a pass, where
+// tile bit 12 is register bit 4 and tile bit 0 lane bit 0: pair j (register
+// bits 0..3) has u = (bit 12 set, bit 0 clear) in the even lane's register
+// j + 16 and w = (bit 0 set, bit 12 clear) in the odd lane's register j.
+__device__ __forceinline__ void xy_wrap(float2 (&v)[32], float t, float s, bool neg) {
+  const bool odd = (threadIdx.x & 1u) != 0u;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const float2 mine = odd ? v[j] : v[j | 16];
+    const float2 other = f2(__shfl_xor_sync(0xffffffffu, mine.x, 1), __shfl_xor_sync(0xffffffffu, mine.y, 1));
+    float2 u = odd ? other : mine, w = odd ? mine : other;
+    xy_gate2(u, w, t, s, neg);
+    if (odd)
+      v[j] = w;
+    else
+      v[j | 16] = u;
+  }
+}
+
+// One XY pass over tiles of 2^13 amplitudes (PL = PlanXyLow: rounds over tile
+// bits 0-4, 4-8, 8-12; PlanXyHigh: 4-8, 8-12), streamed like the forward
+// passes: persistent CTAs, two per SM, one TMA-loaded tile buffer each, the
+// next tile's load issued once the last round's data is in registers, the
+// finished tile stored from registers.  PH: the layer's phase exp(-i g f)
+// first (round 0, before any gate).
+template <class PL, bool PH>
+__global__ void __launch_bounds__(kThreads, 2) k_xy_tma(const __grid_constant__ XyTmaParams P) {
+  constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, SW = 128;
+  static_assert(EB == 5 && (NR == 2 || NR == 3), "XY plans: 32 amplitudes per thread");
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = aligned_base(smem_raw);
+  const Lay L = layout(1u << PL::TB, false, PH);
+  float2 *buf = reinterpret_cast<float2 *>(base);
+  const CostWord *cb = reinterpret_cast<const CostWord *>(base + L.cost_off);
+  float2 *tab = reinterpret_cast<float2 *>(base + L.tab_off);
+  uint64_t *full = reinterpret_cast<uint64_t *>(base + L.bar_off);
+  const int tid = threadIdx.x;
+  const int midbits = P.h - P.c;
+  const float t = P.t, s = P.s;
+  const bool neg = P.neg != 0;
+  __shared__ int s_abort;
+
+  if (PH && P.ph.mode == 0) fill_phase_tab<kThreads>(tab, P.ph);
+  if (tid == 0) {
+    s_abort = 0;
+    mbar_init(full, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto coords = [&](uint64_t T) {
+    const int mid = (int)(T & ((1ull << midbits) - 1ull));
+    TC c;
+    c.x1 = P.c <= 4 ? mid : 0;
+    c.x2 = P.c <= 4 ? 0 : mid;
+    c.x4 = (int)(T >> midbits);
+    return c;
+  };
+  int abort_now = 0;  // uniform over the CTA: read after the tile's first barrier
+  auto read_abort = [&]() { abort_now = s_abort; };
+  auto issue = [&](uint64_t T, bool cost) {
+    const TC c = coords(T);
+    mbar_expect_tx(full, L.tile_bytes + (cost ? L.cost_bytes : 0u));
+    tma_load(buf, &P.map_psi, c, full);
+    if (cost) tma_load(base + L.cost_off, &P.map_cost, c, full);
+  };
+  // the phase reads the costs in round 0: the next tile's costs load at the
+  // first barrier, the state at the release
+  auto cost_next = [&](uint64_t T) {
+    if (tid == 0 && T + gridDim.x < P.ntiles && !abort_now) {
+      mbar_add_tx(full, L.cost_bytes);
+      tma_load(base + L.cost_off, &P.map_cost, coords(T + gridDim.x), full);
+    }
+  };
+  auto release = [&](uint64_t T) {
+    cbar();
+    if (tid == 0 && T + gridDim.x < P.ntiles && !abort_now) issue(T + gridDim.x, false);
+  };
+
+  if (tid == 0 && blockIdx.x < P.ntiles) issue(blockIdx.x, PH);
+
+  int i = 0;
+  for (;; ++i) {
+    const uint64_t T = blockIdx.x + (uint64_t)i * gridDim.x;
+    if (T >= P.ntiles) break;
+    if (abort_now) break;
+    if (!mbar_wait(full, i & 1)) {
+      s_abort = 1;
+      atomicExch(P.err, 1u);
+    }
+    float2 v[NREG];
+    lds_round<PL, 0, SW>(v, buf);
+    if constexpr (PH) phase_round<PL, 0>(v, cb, P.ph, P.cost_kind, tab, f2(1.f, 0.f));
+    xy_round<EB>(v, P.em[0], t, s, neg);
+    if constexpr (PH)
+      xp_hook<PL, 0, 1, SW>(v, buf, [&] { read_abort(); cost_next(T); });
+    else
+      xp_hook<PL, 0, 1, SW>(v, buf, read_abort);
+    if constexpr (NR == 2) release(T);
+    xy_round<EB>(v, P.em[1], t, s, neg);
+    if constexpr (NR == 3) {
+      xp<PL, 1, 2, SW>(v, buf);
+      release(T);
+      xy_round<EB>(v, P.em[2], t, s, neg);
+    }
+    if (P.wrap) xy_wrap(v, t, s, neg);
+    stg_round<PL, NR - 1>(v, P.psi, T, P.h, P.c);
+  }
+  drain(abort_now, full, i);
 }
 
 // ---------------------------------------------------------------- host side
@@ -1498,6 +1657,25 @@ static cudaError_t dispatch_bwd(const TmaBwdParams &P, cudaStream_t s, int nsm) 
   }
 }
 
+template <class PL, bool PH>
+static cudaError_t launch_xy_tma_t(const XyTmaParams &P, cudaStream_t s, int nsm) {
+  const size_t smem = smem_bytes(PL::TB, false, PH);
+  auto kern = k_xy_tma<PL, PH>;
+  static int nb = 0;
+  if (nb == 0) {
+    const size_t mx = smem_bytes(PL::TB, false, true);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    if (e != cudaSuccess) return e;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, mx) != cudaSuccess || b < 1) b = 1;
+    nb = b;
+  }
+  uint64_t grid = (uint64_t)nsm * nb;
+  if (grid > P.ntiles) grid = P.ntiles;
+  kern<<<(unsigned)grid, kThreads, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
 #if QAOA_TMA_CW == 2
 #define QAOA_TMA_FN(name) name##_u16
 #else
@@ -1508,6 +1686,14 @@ cudaError_t QAOA_TMA_FN(launch_fwd_tma)(const TmaFwdParams &P, bool high, cudaSt
   if (P.c < 4 || P.c > 6) return cudaErrorInvalidValue;  // 16- to 64-amplitude segments
   if (!P.psi || ((uintptr_t)P.psi & 15u)) return cudaErrorInvalidValue;
   return high ? dispatch_fwd<PlanTmaF13High>(P, s, nsm) : dispatch_fwd<PlanTmaF13Low>(P, s, nsm);
+}
+
+cudaError_t QAOA_TMA_FN(launch_xy_tma)(const XyTmaParams &P, bool low, cudaStream_t s, int nsm) {
+  if (P.c != 4 || P.h < 4 || !P.psi || ((uintptr_t)P.psi & 15u)) return cudaErrorInvalidValue;
+  if (P.em[0] > 0xF || P.em[1] > 0xF || P.em[2] > 0xF || (!low && P.em[2] != 0)) return cudaErrorInvalidValue;
+  if (low) return P.has_phase ? launch_xy_tma_t<PlanXyLow, true>(P, s, nsm) : launch_xy_tma_t<PlanXyLow, false>(P, s, nsm);
+  if (P.has_phase) return cudaErrorInvalidValue;  // the phase rides on the LOW pass
+  return launch_xy_tma_t<PlanXyHigh, false>(P, s, nsm);
 }
 
 cudaError_t QAOA_TMA_FN(launch_bwd_tma)(const TmaBwdParams &P, bool high, cudaStream_t s, int nsm) {

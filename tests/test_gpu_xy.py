@@ -3,7 +3,10 @@ against the oracle, element by element.  Tolerances as the transverse-field
 forward tests: complex64 2e-5 (state) / 1e-5 (energy), complex128 1e-11 /
 1e-10.  Sizes span one tile (n <= 12), several tiles with passes on low and
 high qubits, and the complete graph's one-gate fallback (pairs no tile
-holds, n > 12)."""
+holds, n > 12).  The complex64 ring from n = 13 runs on register rounds over
+TMA-streamed tiles: n = 13 (the wrap gate in the LOW pass), 14 (a HIGH pass
+whose rows overlap the LOW tile's), 21 and 22 (one and two HIGH passes with
+rows above it), 23 at p = 3."""
 import numpy as np
 import pytest
 
@@ -32,7 +35,8 @@ def test_dicke_state(Q, n, k, st):
 
 @pytest.mark.parametrize("graph", [1, 2])
 @pytest.mark.parametrize("n,st", [(2, "c64"), (3, "c128"), (3, "c64"), (4, "c64"), (9, "c128"), (12, "c64"),
-                                  (13, "c64"), (16, "c64"), (16, "c128"), (19, "c64")])
+                                  (13, "c64"), (14, "c64"), (16, "c64"), (16, "c128"), (19, "c64"),
+                                  (21, "c64"), (22, "c64")])
 def test_simulate_xy_vs_oracle(Q, n, st, graph):
     stype = Q.C64 if st == "c64" else Q.C128
     f = oracle.labs_costs(n).astype(float)
@@ -86,6 +90,24 @@ def test_simulate_xy_other_cost_types(Q, kind):
     psi0 = oracle.dicke(n, n // 2)
     state = Q.dicke_state(n, n // 2)
     state, out = Q.simulate_xy(fd, stats, g, b, state, Q.XY_RING)
+    ref = oracle.simulate_xy(n, f, g, b, psi0, 1)
+    got = dev_np(state).astype(np.complex128)
+    assert np.linalg.norm(got - ref) <= 2e-5 * np.linalg.norm(ref)
+    E = oracle.energy(n, ref, f)
+    assert abs(dev_np(out)[0] - E) <= 1e-5 * max(1.0, abs(E))
+
+
+def test_simulate_xy_ring_deeper(Q):
+    # three layers of the ring at n = 23 (LOW pass and two HIGH passes per
+    # layer; each layer's phase opens its LOW pass after the previous layer's
+    # wrap gate)
+    n, p = 23, 3
+    f = oracle.labs_costs(n).astype(float)
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g, b = I.angles(p, 97, 0, 0.2), I.angles(p, 98)
+    psi0 = oracle.dicke(n, 11)
+    state, out = Q.simulate_xy(fd, stats, g, b, Q.dicke_state(n, 11), Q.XY_RING)
     ref = oracle.simulate_xy(n, f, g, b, psi0, 1)
     got = dev_np(state).astype(np.complex128)
     assert np.linalg.norm(got - ref) <= 2e-5 * np.linalg.norm(ref)
