@@ -629,7 +629,9 @@ def serving_bench(count=1000, nmin=16, nmax=28, loads=(0.5, 0.8, 0.95), graphs_p
                           weights=r["weights"], key=r["key"], want_grad=True)
 
     free, _ = torch.cuda.mem_get_info()
-    arena = int(min(free * 0.6, 96 << 30))
+    # room for several mid-size requests beside the largest one (n = 32 takes
+    # 80 GiB: state, lambda and costs)
+    arena = int(min(free * (0.6 if nmax <= 28 else 0.75), (96 if nmax <= 28 else 176) << 30))
     srv = Q.Server(arena, max_inflight=8)
     for r in reqs[:8]:  # warm the cost-vector cache and the kernels
         srv.wait(sub(srv, r), r["p"])
@@ -639,6 +641,7 @@ def serving_bench(count=1000, nmin=16, nmax=28, loads=(0.5, 0.8, 0.95), graphs_p
         srv.wait(t, r["p"])
     sat_tput = count / (time.perf_counter() - t0)
     srv.close()
+    torch.cuda.empty_cache()
     pct = lambda v, q: float(v[min(len(v) - 1, int(round(q * (len(v) - 1))))])
 
     def open_loop(load):
@@ -659,6 +662,7 @@ def serving_bench(count=1000, nmin=16, nmax=28, loads=(0.5, 0.8, 0.95), graphs_p
             res = srv.wait(t, r["p"])
             lat.append(res["finish_s"] - res["submit_s"])
         srv.close()
+        torch.cuda.empty_cache()
         lat = np.sort(np.array(lat)) * 1000
         # the plain path under the same arrivals: one request at a time, each
         # started at its arrival or when the previous one has finished

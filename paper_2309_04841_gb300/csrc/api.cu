@@ -18,6 +18,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -338,15 +339,30 @@ std::vector<Group> tma_groups(int n, int TB) {
 // four; also n = 21, 29); only as many groups as necessary are cluster pairs.
 // (At n = 21 and 29 a plain plan with one 8-amplitude group has as few
 // groups; measured at n = 29: 114.1 ms per LABS p = 10 evaluation against
-// 108.8 ms with the pair.)
+// 108.8 ms with the pair.)  The environment variable QAOA_ADJOINT_PAIRS
+// overrides the choice: "never" takes the plain plan, "always" makes every
+// HIGH group a cluster pair (for profiling and cross-checks of the pair
+// kernels at any size); unset or anything else is the rule above.
+int adjoint_pairs_mode() {
+  const char *e = getenv("QAOA_ADJOINT_PAIRS");
+  if (!e) return 0;
+  if (!strcmp(e, "never")) return -1;
+  if (!strcmp(e, "always")) return 1;
+  return 0;
+}
+
 std::vector<Group> bwd_groups(int n, int TB) {
   std::vector<Group> plain = tma_groups(n, TB);
   const int c = 4, rows = TB - c;
   const int R = n - TB;  // qubits above the LOW group
-  if (R <= 0) return plain;
+  const int mode = adjoint_pairs_mode();
+  if (R <= 0 || mode < 0) return plain;
   const int k = (R + rows) / (rows + 1);      // HIGH groups, rows + 1 qubits at most each
-  const int ncl = R - rows * k > 0 ? R - rows * k : 0;  // groups that need the extra qubit
-  if (!(1 + k < (int)plain.size())) return plain;
+  int ncl = R - rows * k > 0 ? R - rows * k : 0;  // groups that need the extra qubit
+  if (mode > 0)
+    ncl = k;
+  else if (!(1 + k < (int)plain.size()))
+    return plain;
   std::vector<Group> gs;
   gs.push_back(Group{false, TB, TB, (1u << TB) - 1u});
   int q0 = TB;
@@ -357,12 +373,13 @@ std::vector<Group> bwd_groups(int n, int TB) {
     G.high = true;
     G.c = c;
     G.cl = cl;
-    // local rows h .. h + rows - 1 (and the pair's qubit h + rows); a group
-    // at the top of the range starts lower and rotates only its new qubits
+    // local rows h .. h + rows - 1 (and the pair's qubit h + rows, tile bit
+    // TB); a group at the top of the range starts lower and rotates only its
+    // new qubits
     const int span = rows + (cl ? 1 : 0);
     G.h = q0 + span <= n ? q0 : n - span;
     G.rot = 0;
-    for (int j = c; j < TB; ++j) {
+    for (int j = c; j < TB + (cl ? 1 : 0); ++j) {
       const int q = G.h + j - c;
       if (q >= q0 && q < q0 + len) G.rot |= 1u << j;
     }
@@ -820,12 +837,12 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     P.cost_kind = cost_kind(ct);
     // A cluster pair rotates tile bits 8..11 in round 0 (layout L0), tile
     // bits 4..7 in round 1's registers and tile bit 12 at its lane bit 4
-    // (layout L1, see k_bwd_pair); that fixed set is its sweep.
+    // (layout L1, see k_bwd_pair): the group's new qubits among those.
     Sweep pair_sweep;
     memset(&pair_sweep, 0, sizeof(pair_sweep));
-    pair_sweep.m[0] = 0xF;
-    pair_sweep.m[1] = 0xF;
-    pair_sweep.lm[1] = 0x10;
+    pair_sweep.m[0] = (uint8_t)((G.rot >> 8) & 0xFu);
+    pair_sweep.m[1] = (uint8_t)((G.rot >> 4) & 0xFu);
+    pair_sweep.lm[1] = (uint8_t)(((G.rot >> TB) & 1u) << 4);
     P.cluster = G.cl;
     P.s1 = G.cl ? pair_sweep : G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
     {

@@ -118,6 +118,7 @@ struct Job {
   CostKey ckey;
   bool holds_cost = false;
   int unit = -1;  // running unit index
+  int bypassed = 0;  // later jobs admitted while this one waited for memory
 };
 
 // A unit of GPU work: one large job, or one batch of small jobs, on a stream.
@@ -450,6 +451,8 @@ void reap(qaoa_server *S) {
   }
 }
 
+constexpr int kMaxBypass = 8;
+
 void worker_main(qaoa_server *S) {
   cudaSetDevice(S->device);
   std::unique_lock<std::mutex> lk(S->mu);
@@ -465,8 +468,12 @@ void worker_main(qaoa_server *S) {
       if (u >= 0 && start_small_batch(S, small, u)) progressed = true;
     }
     // large jobs in arrival order; later ones may pass an earlier one that
-    // does not fit yet (bounded look-ahead)
+    // does not fit yet (bounded look-ahead), but each waiting job lets at
+    // most kMaxBypass pass it: after that nothing more is admitted behind it
+    // until the running work has freed enough memory for it (no starvation
+    // of the largest requests)
     int looked = 0;
+    std::vector<Job *> skipped;
     for (auto it = S->pending.begin(); it != S->pending.end() && looked < 64;) {
       Job *j = *it;
       if (j->n <= kSmallMaxN && j->p <= kSmallMaxLayers) {
@@ -477,9 +484,12 @@ void worker_main(qaoa_server *S) {
       const int u = free_unit(S);
       if (u < 0) break;
       if (start_large(S, j, u)) {
+        for (Job *k : skipped) ++k->bypassed;
         it = S->pending.erase(it);
         progressed = true;
       } else {
+        if (j->bypassed >= kMaxBypass) break;
+        skipped.push_back(j);
         ++it;
       }
     }

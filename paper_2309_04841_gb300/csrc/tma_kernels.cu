@@ -1063,6 +1063,32 @@ __device__ __forceinline__ void pair_xchg2(const float2 (&v)[PL::NREG], const fl
   }
 }
 
+// Round 1 back to L0: local position 8 is lane bit 4 there, so a thread
+// keeps all its values or pushes all of them; one branch per thread rather
+// than one per register (half of each warp on either side).
+template <class PL>
+__device__ __forceinline__ void pair_xchg_lane(const float2 (&v)[PL::NREG], const float2 (&w)[PL::NREG],
+                                               float2 *bv, float2 *bw, uint32_t rbv, uint32_t rbw,
+                                               uint32_t rbar, uint32_t rank) {
+  static_assert((PL::lane(1) & 0x100u) && !(PL::reg(1) & 0x100u), "position 8 a lane bit of round 1");
+  const uint32_t tt = thr_tile<PL, 1>();
+  if (((tt >> 8) & 1u) == rank) {
+#pragma unroll
+    for (int r = 0; r < PL::NREG; ++r) {
+      const uint32_t o = tswz<128>(tt | pdep(r, PL::reg(1)));
+      bv[o] = v[r];
+      bw[o] = w[r];
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < PL::NREG; ++r) {
+      const uint32_t o = tswz<128>((tt ^ 0x100u) | pdep(r, PL::reg(1))) * 8u;
+      st_async(rbv + o, v[r], rbar);
+      st_async(rbw + o, w[r], rbar);
+    }
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(kThreads, 2) k_bwd_pair(const __grid_constant__ TmaBwdParams P) {
   using PL = PlanTmaB12High;
@@ -1213,7 +1239,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_pair(const __grid_constant_
       // L1 -> L0
       const bool fr2 = mbar_wait_cl(&xbar[2], par);
       flag(fr2);
-      if (fr2) pair_xchg2<PL, 1>(v, w, bv, bw, remote(bv), remote(bw), remote(&xbar[3]), rank);
+      if (fr2) pair_xchg_lane<PL>(v, w, bv, bw, remote(bv), remote(bw), remote(&xbar[3]), rank);
       cbar();
       if constexpr (PH && early_cost) cost_next(U);
       flag(mbar_wait_cl(&xbar[3], par));
@@ -1705,12 +1731,18 @@ cudaError_t QAOA_TMA_FN(launch_bwd_tma)(const TmaBwdParams &P, bool high, cudaSt
         __builtin_popcount(P.s2.lm[r]) > 1)
       return cudaErrorInvalidValue;
   if (P.cluster) {
-    // a 9-qubit HIGH group on a pair: 16-amplitude segments, the full
-    // rotation set of the two layouts, an even number of local tiles
+    // a HIGH group of up to 9 qubits on a pair: 16-amplitude segments,
+    // rotations within the two layouts' sets (round 0: 4 register bits;
+    // round 1: 4 register bits and lane bit 4), the same set in both
+    // sweeps, an even number of local tiles
     const bool s2 = (P.s2.m[0] | P.s2.m[1] | P.s2.lm[1]) != 0;
-    if (!high || P.c != 4 || P.h < 4 || P.ntiles < 2 || (P.ntiles & 1) || P.s1.m[0] != 0xF ||
-        P.s1.m[1] != 0xF || P.s1.lm[0] != 0 || P.s1.lm[1] != 0x10 || P.s1.m[2] != 0 ||
-        (s2 && (P.s2.m[0] != 0xF || P.s2.m[1] != 0xF || P.s2.lm[0] != 0 || P.s2.lm[1] != 0x10)))
+    auto in_set = [](const Sweep &w) {
+      return (w.m[0] & ~0xFu) == 0 && (w.m[1] & ~0xFu) == 0 && w.m[2] == 0 && w.m[3] == 0 &&
+             w.lm[0] == 0 && (w.lm[1] & ~0x10u) == 0 && w.lm[2] == 0 && w.lm[3] == 0 &&
+             (w.m[0] | w.m[1] | w.lm[1]) != 0;
+    };
+    if (!high || P.c != 4 || P.h < 4 || P.ntiles < 2 || (P.ntiles & 1) || !in_set(P.s1) ||
+        (s2 && (P.s2.m[0] != P.s1.m[0] || P.s2.m[1] != P.s1.m[1] || P.s2.lm[1] != P.s1.lm[1])))
       return cudaErrorInvalidValue;
     return dispatch_bwd_pair(P, s, nsm);
   }

@@ -568,9 +568,11 @@ class Server:
         return {k: getattr(st, k) for k, _ in ServerStats._fields_}
 
     def close(self):
+        """Destroy the server (it drains first) and drop the arena."""
         if self._h:
             lib().qaoa_server_destroy(self._h)
             self._h = C.c_void_p()
+        self.arena = None
 
     def __del__(self):
         try:

@@ -77,6 +77,49 @@ def test_grad_cluster_pair_vs_oracle(Q, cost, n, p):
     assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < 1e-4
 
 
+@pytest.mark.parametrize("n,p", [(13, 2), (17, 3), (22, 2), (24, 2)])
+def test_grad_forced_pairs_vs_oracle(Q, monkeypatch, n, p):
+    # every HIGH group of the adjoint on a cluster pair, including groups that
+    # rotate only some of the pair's 9 qubits: n = 13 only the split qubit,
+    # n = 17 the round-0 bits and the split qubit, n = 22 a full pair then the
+    # split qubit alone, n = 24 a full pair then three qubits
+    monkeypatch.setenv("QAOA_ADJOINT_PAIRS", "always")
+    f = oracle.labs_costs(n).astype(float)
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g = I.angles(p, 50 + n, 0, 0.2)
+    b = I.angles(p, 51 + n)
+    Q.profile_enable(True)
+    try:
+        Q.profile_read()
+        out = dev_np(Q.grad(fd, stats, g, b))
+        kinds = Q.profile_read()
+    finally:
+        Q.profile_enable(False)
+    assert any(k.startswith("bwd_pair") for k in kinds) and not any(k.startswith("bwd_high") for k in kinds)
+    E, dg, db = oracle.grad(n, f, g, b)
+    assert abs(out[0] - E) <= 1e-5 * max(1.0, abs(E))
+    assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < 1e-4
+
+
+def test_grad_pair_plans_agree_n26(Q, monkeypatch):
+    # the same gradient from the plain adjoint plan and from the plan with
+    # every HIGH group on a cluster pair (n = 26: {12-20}, {17-25} rotating
+    # 21-25), both in complex64: agreement to rounding
+    n, p = 26, 3
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g = I.angles(p, 6, 0, 0.3)
+    b = I.angles(p, 16)
+    res = {}
+    for mode in ("never", "always"):
+        monkeypatch.setenv("QAOA_ADJOINT_PAIRS", mode)
+        res[mode] = dev_np(Q.grad(fd, stats, g, b))
+    a, c = res["never"], res["always"]
+    assert abs(a[0] - c[0]) <= 1e-6 * abs(a[0])
+    assert rel(c[2:], a[2:]) < 1e-5
+
+
 @pytest.mark.parametrize("n,p", [(10, 5), (16, 6)])
 def test_grad_vs_oracle_weighted_maxcut(Q, n, p):
     w = I.workload("maxcut3w28_p40", n=n)
