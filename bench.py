@@ -207,6 +207,21 @@ def traffic_record(n, p):
     return rec.get("kernels")
 
 
+def cost_build_line(n, N, ms):
+    """The LABS cost-vector build against the popcount rate: n - 1 popcounts
+    per element (one per shift k), at 16 per clock per SM (the CUDA
+    arithmetic-throughput table's figure for 32-bit population count) and the
+    maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = 16.0 * sms * 2.07e9 / 1e9
+    rate = (n - 1) * N / (ms * 1e-3) / 1e9
+    return {"kernel": "k_labs (LABS cost vector, int32), outside the timed region", "ms": ms,
+            "Gelements_per_s": N / (ms * 1e-3) / 1e9, "bound": "alu", "unit": "Gpopc/s",
+            "achieved": rate, "peak": peak, "frac": rate / peak,
+            "peak_source": f"16 popc per clock per SM x {sms} SMs x 2070 MHz (maximum SM clock)"}
+
+
 def sweep_split(prof, steps):
     """Per-step device time (ms) and pass bytes of the forward ("fwd_*") and
     adjoint ("bwd_*") launches."""
@@ -402,6 +417,7 @@ def run_ours(a, ws, rank, local):
             "kinds": eff},
         "kernel_groups": group_kinds(kinds, a.steps),
         "precompute_ms": precompute_ms,
+        "cost_build": cost_build_line(n, N, precompute_ms),
         "result": {"energy": float(result[0]), "overlap": float(result[1]),
                    "uncompute_drift": drift},
     }

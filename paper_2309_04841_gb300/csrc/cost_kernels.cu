@@ -64,16 +64,19 @@ __global__ void __launch_bounds__(256) k_terms(const __grid_constant__ TermChunk
 }
 
 // LABS: f(x) = sum_{k=1}^{n-1} C_k^2, C_k = (n - k) - 2 popc((x ^ x >> k) & (2^{n-k} - 1)):
-// the aperiodic autocorrelation counts agreeing minus disagreeing pairs.
-template <typename T>
-__global__ void __launch_bounds__(256) k_labs(int n, T *out) {
-  const uint64_t N = 1ull << n;
+// the aperiodic autocorrelation counts agreeing minus disagreeing pairs.  n is
+// a template argument, so the k loop unrolls with constant shifts and masks
+// (per k: shift, xor-and, popc and two integer multiply-adds).
+template <typename T, int NQ>
+__global__ void __launch_bounds__(256) k_labs(T *out) {
+  constexpr uint64_t N = 1ull << NQ;
   for (uint64_t x = blockIdx.x * 256ull + threadIdx.x; x < N; x += (uint64_t)gridDim.x * 256ull) {
     const uint32_t xi = (uint32_t)x;
     int32_t f = 0;
-    for (int k = 1; k < n; ++k) {
-      const uint32_t m = (n - k >= 32) ? 0xffffffffu : ((1u << (n - k)) - 1u);
-      const int32_t c = (n - k) - 2 * __popc((xi ^ (xi >> k)) & m);
+#pragma unroll
+    for (int k = 1; k < NQ; ++k) {
+      const uint32_t m = (NQ - k >= 32) ? 0xffffffffu : ((1u << (NQ - k)) - 1u);
+      const int32_t c = (NQ - k) - 2 * __popc((xi ^ (xi >> k)) & m);
       f += c * c;
     }
     out[x] = (T)f;
@@ -475,14 +478,32 @@ cudaError_t launch_terms(const TermChunk &P, cudaStream_t s, int nsm) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_labs(int n, int32_t *out, cudaStream_t s, int nsm) {
-  k_labs<int32_t><<<grid_for(n, nsm, 8), 256, 0, s>>>(n, out);
+template <typename T>
+static cudaError_t launch_labs_t(int n, T *out, cudaStream_t s, int nsm) {
+  const unsigned grid = grid_for(n, nsm, 8);
+  switch (n) {
+#define QAOA_LABS_CASE(NQ) \
+  case NQ:                 \
+    k_labs<T, NQ><<<grid, 256, 0, s>>>(out); \
+    break;
+    QAOA_LABS_CASE(2) QAOA_LABS_CASE(3) QAOA_LABS_CASE(4) QAOA_LABS_CASE(5) QAOA_LABS_CASE(6)
+    QAOA_LABS_CASE(7) QAOA_LABS_CASE(8) QAOA_LABS_CASE(9) QAOA_LABS_CASE(10) QAOA_LABS_CASE(11)
+    QAOA_LABS_CASE(12) QAOA_LABS_CASE(13) QAOA_LABS_CASE(14) QAOA_LABS_CASE(15) QAOA_LABS_CASE(16)
+    QAOA_LABS_CASE(17) QAOA_LABS_CASE(18) QAOA_LABS_CASE(19) QAOA_LABS_CASE(20) QAOA_LABS_CASE(21)
+    QAOA_LABS_CASE(22) QAOA_LABS_CASE(23) QAOA_LABS_CASE(24) QAOA_LABS_CASE(25) QAOA_LABS_CASE(26)
+    QAOA_LABS_CASE(27) QAOA_LABS_CASE(28) QAOA_LABS_CASE(29) QAOA_LABS_CASE(30) QAOA_LABS_CASE(31)
+    QAOA_LABS_CASE(32)
+#undef QAOA_LABS_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
+cudaError_t launch_labs(int n, int32_t *out, cudaStream_t s, int nsm) { return launch_labs_t(n, out, s, nsm); }
+
 cudaError_t launch_labs_u16(int n, uint16_t *out, cudaStream_t s, int nsm) {
-  k_labs<uint16_t><<<grid_for(n, nsm, 8), 256, 0, s>>>(n, out);
-  return cudaGetLastError();
+  return launch_labs_t(n, out, s, nsm);
 }
 
 cudaError_t launch_convert(int n, const void *src, int src_kind, void *dst, int dst_kind,
