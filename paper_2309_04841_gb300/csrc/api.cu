@@ -174,6 +174,7 @@ void make_phase(PhaseData<Real> &ph, double g, qaoa_cost_type ct, const qaoa_cos
     ph.g_hi = (float)g2;
     ph.g_lo = (float)(g2 - (double)ph.g_hi);
   }
+  ph.scl = (Real)(ph.mode == 1 ? scale.real() : 1.0);  // the tiled passes fold only real scales
 }
 
 // Digit tables of exp(-i g f) for the TMA passes (layout in PhaseDigits).
@@ -577,6 +578,34 @@ std::vector<PassOp> adjoint_schedule(int k, int p) {
   return ops;
 }
 
+// Reduced form of exp(-i b X) for the tiled passes (rot_tan): the form with
+// |t| <= 1 and the real factor it drops.
+struct RedRot {
+  double t;
+  int form;
+  double sigma;
+};
+
+RedRot red_rot(double b) {
+  const double c = cos(b), s = sin(b);
+  if (fabs(c) >= fabs(s)) return RedRot{s / c, 0, c};
+  return RedRot{c / s, 1, s};
+}
+
+double ipow_d(double x, int k) {
+  double r = 1.0;
+  for (int i = 0; i < k; ++i) r *= x;
+  return r;
+}
+
+int sweep_qubits(const Sweep &w) {
+  int k = 0;
+  for (int r = 0; r < 4; ++r) k += __builtin_popcount((unsigned)w.m[r]);
+  return k;
+}
+
+int popc8(uint8_t m) { return __builtin_popcount((unsigned)m); }
+
 template <typename Real>
 qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
                           const double *gam, const double *bet, int p, void *state, int init_plus,
@@ -590,6 +619,9 @@ qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa
   const int nsm = num_sms();
   if (d_out) CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
   FwdParams<Real> P;
+  // the stored state is the true one divided by sig (the dropped factors of
+  // the reduced rotations); the next phase, or the last pass, multiplies it back
+  double sig = 1.0;
   for (const PassOp &op : ops) {
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
@@ -601,17 +633,29 @@ qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa
     // (these plans hold every rotated bit in registers: no lane rotations)
     if (op.l1 >= 0) {
       P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
-      P.c1 = (Real)cos(bet[op.l1]);
-      P.s1s = (Real)sin(bet[op.l1]);
+      const RedRot R = red_rot(bet[op.l1]);
+      P.t1 = (Real)R.t;
+      P.form1 = R.form;
+      sig *= ipow_d(R.sigma, sweep_qubits(P.s1));
     }
     if (op.l2 >= 0) {
       P.s2 = G.high ? make_sweep<High>(G.rot, !two) : make_sweep<Low>(G.rot, !two);
-      P.c2 = (Real)cos(bet[op.l2]);
-      P.s2s = (Real)sin(bet[op.l2]);
+      const RedRot R = red_rot(bet[op.l2]);
+      P.t2 = (Real)R.t;
+      P.form2 = R.form;
     }
     if (uses_lanes(P.s1) || uses_lanes(P.s2)) return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
     P.has_phase = op.lp >= 0;
-    if (P.has_phase) make_phase<Real>(P.ph, gam[op.lp], ct, stats);
+    if (P.has_phase) {  // s1 runs before the phase, s2 after it
+      make_phase<Real>(P.ph, gam[op.lp], ct, stats, sig);
+      sig = 1.0;
+    }
+    if (op.l2 >= 0) sig *= ipow_d(red_rot(bet[op.l2]).sigma, sweep_qubits(P.s2));
+    P.post_scale = (Real)1;
+    if (&op == &ops.back()) {
+      P.post_scale = (Real)sig;
+      sig = 1.0;
+    }
     P.init_plus = op.init;
     P.amp = (Real)(1.0 / sqrt(ldexp(1.0, n)));
     P.reduce = op.reduce;
@@ -643,6 +687,7 @@ qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qao
   const int nsm = num_sms();
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
   BwdParams<Real> P;
+  double sig = 1.0;
   for (const PassOp &op : ops) {
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
@@ -651,20 +696,42 @@ qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qao
     P.cost = cost;
     P.cost_kind = cost_kind(ct);
     P.g = make_geom(n, G, TB);
+    // psi and lambda are stored divided by sig; un-rotations are the reduced
+    // forms of exp(-i (-beta) X)
     P.s1 = G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
-    P.c1 = (Real)cos(bet[op.l1]);
-    P.s1s = (Real)-sin(bet[op.l1]);
+    {
+      const RedRot R = red_rot(-bet[op.l1]);
+      P.t1 = (Real)R.t;
+      P.form1 = R.form;
+      for (int r = 0; r < Low::NR; ++r) {  // the kernel walks s1 upward
+        P.w1[r] = (Real)(sig * sig);
+        sig *= ipow_d(R.sigma, popc8(P.s1.m[r]));
+      }
+    }
     P.out_b1 = d_grad_b + op.l1;
     if (op.lp >= 0) {
       P.has_phase = 1;
-      make_phase<Real>(P.ph, -gam[op.lp], ct, stats);
+      P.wg = (Real)(sig * sig);
+      make_phase<Real>(P.ph, -gam[op.lp], ct, stats, sig);  // the un-phase pays the pending scale
+      sig = 1.0;
       P.out_g = d_grad_g + op.lp;
     }
     if (op.l2 >= 0) {
       P.s2 = G.high ? make_sweep<High>(G.rot, false) : make_sweep<Low>(G.rot, false);
-      P.c2 = (Real)cos(bet[op.l2]);
-      P.s2s = (Real)-sin(bet[op.l2]);
+      const RedRot R = red_rot(-bet[op.l2]);
+      P.t2 = (Real)R.t;
+      P.form2 = R.form;
+      for (int k = 0; k < Low::NR; ++k) {  // and s2 downward
+        const int r = Low::NR - 1 - k;
+        P.w2[r] = (Real)(sig * sig);
+        sig *= ipow_d(R.sigma, popc8(P.s2.m[r]));
+      }
       P.out_b2 = d_grad_b + op.l2;
+    }
+    P.post_scale = (Real)1;
+    if (&op == &ops.back()) {
+      P.post_scale = (Real)sig;
+      sig = 1.0;
     }
     if (uses_lanes(P.s1) || uses_lanes(P.s2))
       return fail(QAOA_ERR_INVALID_ARG, "internal: plan needs lane rotations");
@@ -721,8 +788,6 @@ TanRot tan_rot(double beta, bool adjoint) {
   }
   return r;
 }
-
-int popc8(uint8_t m) { return __builtin_popcount((unsigned)m); }
 
 float2 f2c(std::complex<double> z) { return make_float2((float)z.real(), (float)z.imag()); }
 

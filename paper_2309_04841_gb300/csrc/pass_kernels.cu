@@ -35,12 +35,27 @@ __device__ __forceinline__ C2 cmul(C2 a, C2 b) {
   return mk<C2>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// (a, b) <- (c a - i s b, -i s a + c b): exp(-i beta X) on one amplitude pair
-// with c = cos beta, s = sin beta (Algorithm 1, a = cos b, b = -i sin b).
-template <typename C2, typename Real>
-__device__ __forceinline__ void rotx(C2 &a, C2 &b, Real c, Real s) {
-  const C2 na = mk<C2>(c * a.x + s * b.y, c * a.y - s * b.x);
-  const C2 nb = mk<C2>(c * b.x + s * a.y, c * b.y - s * a.x);
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+
+// exp(-i b X) on one amplitude pair (Algorithm 1 with a = cos b, b = -i sin b)
+// divided by a real factor, so that each component takes one fused
+// multiply-add: form 0, factor cos b, t = tan b:
+//   (a, b) <- (a - i t b, b - i t a);
+// form 1, factor sin b, t = cot b:
+//   (a, b) <- (t a - i b, t b - i a).
+// The host picks the form with |t| <= 1 and carries the product of the
+// dropped factors (PassOp scales in the tiled schedules).
+template <int FORM, typename C2, typename Real>
+__device__ __forceinline__ void rot_tan(C2 &a, C2 &b, Real t) {
+  C2 na, nb;
+  if constexpr (FORM == 0) {
+    na = mk<C2>(fmx(t, b.y, a.x), fmx(-t, b.x, a.y));
+    nb = mk<C2>(fmx(t, a.y, b.x), fmx(-t, a.x, b.y));
+  } else {
+    na = mk<C2>(fmx(t, a.x, b.y), fmx(t, a.y, -b.x));
+    nb = mk<C2>(fmx(t, b.x, a.y), fmx(t, b.y, -a.x));
+  }
   a = na;
   b = nb;
 }
@@ -101,39 +116,54 @@ __device__ __forceinline__ void xpose2(C2 (&v)[PL::NREG], C2 (&w)[PL::NREG], C2 
   }
 }
 
-template <int EB, typename C2, typename Real>
-__device__ __forceinline__ void rot_regs(C2 (&v)[1 << EB], uint32_t m, Real c, Real s) {
+template <int EB, int FORM, typename C2, typename Real>
+__device__ __forceinline__ void rot_regs_f(C2 (&v)[1 << EB], uint32_t m, Real t) {
 #pragma unroll
   for (int i = 0; i < EB; ++i) {
     if ((m >> i) & 1u) {
 #pragma unroll
       for (int r = 0; r < (1 << EB); ++r)
-        if (!((r >> i) & 1)) rotx(v[r], v[r | (1 << i)], c, s);
+        if (!((r >> i) & 1)) rot_tan<FORM>(v[r], v[r | (1 << i)], t);
     }
   }
 }
 
+template <int EB, typename C2, typename Real>
+__device__ __forceinline__ void rot_regs(C2 (&v)[1 << EB], uint32_t m, Real t, int form) {
+  if (form == 0)
+    rot_regs_f<EB, 0>(v, m, t);
+  else
+    rot_regs_f<EB, 1>(v, m, t);
+}
+
 // Un-rotate psi (v) and lambda (w) on the masked register bits, first adding
-// Im[conj(l_a) p_b + conj(l_b) p_a] = Im <lambda| X_q |psi> restricted to the
-// pair (the value is the same before or after any common X rotation).
+// Im[conj(l_a) p_b + conj(l_b) p_a] = Im <lambda| X_q |psi> of every masked
+// pair: the value does not change under common X rotations, and taking all of
+// them before the round's rotations puts them at one scale, which wgt (the
+// round's sigma^2) converts back.
 template <int EB, typename C2, typename Real>
 __device__ __forceinline__ void unrot_regs_acc(C2 (&v)[1 << EB], C2 (&w)[1 << EB], uint32_t m,
-                                               Real c, Real s, Real &acc) {
+                                               Real t, int form, Real wgt, Real &acc) {
+  Real g[2] = {0, 0};
 #pragma unroll
   for (int i = 0; i < EB; ++i) {
     if ((m >> i) & 1u) {
 #pragma unroll
       for (int r = 0; r < (1 << EB); ++r) {
         if (!((r >> i) & 1)) {
-          C2 &pa = v[r], &pb = v[r | (1 << i)];
-          C2 &la = w[r], &lb = w[r | (1 << i)];
-          acc += la.x * pb.y - la.y * pb.x + lb.x * pa.y - lb.y * pa.x;
-          rotx(pa, pb, c, s);
-          rotx(la, lb, c, s);
+          const C2 pa = v[r], pb = v[r | (1 << i)], la = w[r], lb = w[r | (1 << i)];
+          const int k = (r >> (i == 0 ? 1 : 0)) & 1;
+          g[k] = fmx(la.x, pb.y, g[k]);
+          g[k] = fmx(-la.y, pb.x, g[k]);
+          g[k] = fmx(lb.x, pa.y, g[k]);
+          g[k] = fmx(-lb.y, pa.x, g[k]);
         }
       }
     }
   }
+  acc = fmx(g[0] + g[1], wgt, acc);
+  rot_regs<EB>(v, m, t, form);
+  rot_regs<EB>(w, m, t, form);
 }
 
 // Cost value as a float pair hi + lo (exact for int32 and float32 costs,
@@ -185,7 +215,7 @@ __device__ __forceinline__ float2 phase_factor(const PhaseData<float> &ph, const
   const float r = (p - rintf(p)) + (e + fmaf(ph.g_hi, fl, ph.g_lo * fh));
   float sn, cs;
   sincospif(2.0f * r, &sn, &cs);
-  return make_float2(cs, -sn);
+  return make_float2(cs * ph.scl, -sn * ph.scl);
 }
 
 __device__ __forceinline__ double2 phase_factor(const PhaseData<double> &ph, const double2 *tlo,
@@ -202,7 +232,7 @@ __device__ __forceinline__ double2 phase_factor(const PhaseData<double> &ph, con
   const double r = t - rint(t);
   double sn, cs;
   sincospi(2.0 * r, &sn, &cs);
-  return make_double2(cs, -sn);
+  return make_double2(cs * ph.scl, -sn * ph.scl);
 }
 
 template <class PL, int R, typename Real, typename C2>
@@ -339,36 +369,40 @@ __global__ void __launch_bounds__(PL::NT, 2) k_fwd(const __grid_constant__ FwdPa
     }
     bool final0;
     if (has1) {
-      rot_regs<EB>(v, P.s1.m[0], P.c1, P.s1s);
+      rot_regs<EB>(v, P.s1.m[0], P.t1, P.form1);
       xpose<PL, 0, 1>(v, tile);
-      rot_regs<EB>(v, P.s1.m[1], P.c1, P.s1s);
+      rot_regs<EB>(v, P.s1.m[1], P.t1, P.form1);
       if constexpr (NR == 3) {
         xpose<PL, 1, 2>(v, tile);
-        rot_regs<EB>(v, P.s1.m[2], P.c1, P.s1s);
+        rot_regs<EB>(v, P.s1.m[2], P.t1, P.form1);
       }
       if (P.has_phase) apply_phase<PL, NR - 1>(v, P.ph, tlo, thi, P.cost, P.cost_kind, g, base);
       if (has2) {
-        rot_regs<EB>(v, P.s2.m[NR - 1], P.c2, P.s2s);
+        rot_regs<EB>(v, P.s2.m[NR - 1], P.t2, P.form2);
         if constexpr (NR == 3) {
           xpose<PL, 2, 1>(v, tile);
-          rot_regs<EB>(v, P.s2.m[1], P.c2, P.s2s);
+          rot_regs<EB>(v, P.s2.m[1], P.t2, P.form2);
         }
         xpose<PL, 1, 0>(v, tile);
-        rot_regs<EB>(v, P.s2.m[0], P.c2, P.s2s);
+        rot_regs<EB>(v, P.s2.m[0], P.t2, P.form2);
         final0 = true;
       } else {
         final0 = false;
       }
     } else {
       if (P.has_phase) apply_phase<PL, 0>(v, P.ph, tlo, thi, P.cost, P.cost_kind, g, base);
-      rot_regs<EB>(v, P.s2.m[0], P.c2, P.s2s);
+      rot_regs<EB>(v, P.s2.m[0], P.t2, P.form2);
       xpose<PL, 0, 1>(v, tile);
-      rot_regs<EB>(v, P.s2.m[1], P.c2, P.s2s);
+      rot_regs<EB>(v, P.s2.m[1], P.t2, P.form2);
       if constexpr (NR == 3) {
         xpose<PL, 1, 2>(v, tile);
-        rot_regs<EB>(v, P.s2.m[2], P.c2, P.s2s);
+        rot_regs<EB>(v, P.s2.m[2], P.t2, P.form2);
       }
       final0 = false;
+    }
+    if (P.post_scale != (Real)1) {
+#pragma unroll
+      for (int r = 0; r < NREG; ++r) v[r] = mk<C2>(v[r].x * P.post_scale, v[r].y * P.post_scale);
     }
     if (P.reduce) {
       Real e = 0, o = 0;
@@ -438,35 +472,37 @@ __global__ void __launch_bounds__(PL::NT, 2) k_bwd(const __grid_constant__ BwdPa
     }
     Real a1 = 0, ag = 0, a2 = 0;
     // sweep 1 ascending through the rounds
-    unrot_regs_acc<EB>(v, w, P.s1.m[0], P.c1, P.s1s, a1);
+    unrot_regs_acc<EB>(v, w, P.s1.m[0], P.t1, P.form1, P.w1[0], a1);
     xpose2<PL, 0, 1>(v, w, tv, tw);
-    unrot_regs_acc<EB>(v, w, P.s1.m[1], P.c1, P.s1s, a1);
+    unrot_regs_acc<EB>(v, w, P.s1.m[1], P.t1, P.form1, P.w1[1], a1);
     if constexpr (NR == 3) {
       xpose2<PL, 1, 2>(v, w, tv, tw);
-      unrot_regs_acc<EB>(v, w, P.s1.m[2], P.c1, P.s1s, a1);
+      unrot_regs_acc<EB>(v, w, P.s1.m[2], P.t1, P.form1, P.w1[2], a1);
     }
     if (P.has_phase) {
       // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
       const uint64_t xt = base + tile_off(g, thr_toff<PL, NR - 1>());
+      Real raw = 0;
 #pragma unroll
       for (int r = 0; r < NREG; ++r) {
         const uint64_t x = xt + tile_off(g, pdep(r, PL::reg(NR - 1)));
         const Real f = (Real)cost_d(P.cost, P.cost_kind, x);
-        ag += f * (w[r].x * v[r].y - w[r].y * v[r].x);
+        raw += f * (w[r].x * v[r].y - w[r].y * v[r].x);
         const C2 ph = phase_factor(P.ph, tlo, thi, P.cost, P.cost_kind, x);
         v[r] = cmul(v[r], ph);
         w[r] = cmul(w[r], ph);
       }
+      ag = raw * P.wg;
     }
     bool final0 = false;
     if (has2) {
-      unrot_regs_acc<EB>(v, w, P.s2.m[NR - 1], P.c2, P.s2s, a2);
+      unrot_regs_acc<EB>(v, w, P.s2.m[NR - 1], P.t2, P.form2, P.w2[NR - 1], a2);
       if constexpr (NR == 3) {
         xpose2<PL, 2, 1>(v, w, tv, tw);
-        unrot_regs_acc<EB>(v, w, P.s2.m[1], P.c2, P.s2s, a2);
+        unrot_regs_acc<EB>(v, w, P.s2.m[1], P.t2, P.form2, P.w2[1], a2);
       }
       xpose2<PL, 1, 0>(v, w, tv, tw);
-      unrot_regs_acc<EB>(v, w, P.s2.m[0], P.c2, P.s2s, a2);
+      unrot_regs_acc<EB>(v, w, P.s2.m[0], P.t2, P.form2, P.w2[0], a2);
       final0 = true;
     }
     (void)has1;
@@ -476,6 +512,13 @@ __global__ void __launch_bounds__(PL::NT, 2) k_bwd(const __grid_constant__ BwdPa
       P.partials[T * 3 + 0] = a[0];
       P.partials[T * 3 + 1] = a[1];
       P.partials[T * 3 + 2] = a[2];
+    }
+    if (P.post_scale != (Real)1) {
+#pragma unroll
+      for (int r = 0; r < NREG; ++r) {
+        v[r] = mk<C2>(v[r].x * P.post_scale, v[r].y * P.post_scale);
+        w[r] = mk<C2>(w[r].x * P.post_scale, w[r].y * P.post_scale);
+      }
     }
     if (final0) {
       store_tile<PL, 0>(v, P.psi, g, base);

@@ -133,6 +133,7 @@ struct PhaseData {
   int nhi;      // entries of T_hi in use
   float g_hi, g_lo;  // complex64 computed mode: g / 2pi = g_hi + g_lo
   double g2pi;       // complex128 computed mode: g / 2pi
+  Real scl;          // computed mode: factor applied with the phase (tables carry it in T_hi)
   C2 tab_lo[256];
   C2 tab_hi[256];
 };
@@ -145,7 +146,12 @@ struct FwdParams {
   int cost_kind;
   Geom g;
   Sweep s1, s2;         // s1 before the phase, s2 after
-  Real c1, s1s, c2, s2s;  // cos/sin of the two sweeps' beta
+  // the sweeps' rotations in reduced form (rot_tan): multiplier and form;
+  // the state is stored divided by the product of the dropped factors, which
+  // the host folds into the next phase or into post_scale
+  Real t1, t2;
+  int form1, form2;
+  Real post_scale;      // the pass's result times this before the reduction and the store
   int has_phase;
   int init_plus;        // ignore psi, start from |+>
   Real amp;             // 2^{-n/2}
@@ -165,7 +171,13 @@ struct BwdParams {
   int cost_kind;
   Geom g;
   Sweep s1, s2;
-  Real c1, s1s, c2, s2s;  // un-rotation coefficients (cos b, -sin b)
+  Real t1, t2;            // un-rotations in reduced form (rot_tan of -beta)
+  int form1, form2;
+  // psi and lambda are stored divided by a common real factor sigma; a raw
+  // inner product is the true one divided by sigma^2, so each round's sum is
+  // weighted by that round's sigma^2 (w1 / w2 per round, wg for the phase)
+  Real w1[3], w2[3], wg;
+  Real post_scale;        // psi and lambda times this before the store
   int has_phase;          // g_gamma accumulation + un-phase between sweeps
   int init_lambda;        // lambda <- f psi at load
   double *partials;       // [ntiles][3]
