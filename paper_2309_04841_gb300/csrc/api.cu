@@ -606,13 +606,11 @@ int sweep_qubits(const Sweep &w) {
 
 int popc8(uint8_t m) { return __builtin_popcount((unsigned)m); }
 
-template <typename Real>
-qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
-                          const double *gam, const double *bet, int p, void *state, int init_plus,
-                          const Ws &ws, double *d_out, cudaStream_t s) {
+template <typename Real, class Low, class High>
+qaoa_status tiled_forward_pl(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                             const double *gam, const double *bet, int p, void *state, int init_plus,
+                             const Ws &ws, double *d_out, cudaStream_t s) {
   using C2 = typename C2T<Real>::type;
-  using Low = typename FwdTB<Real>::Low;
-  using High = typename FwdTB<Real>::High;
   const int TB = Low::TB;
   const std::vector<Group> gs = plan_groups(n, TB, kHighC);
   const std::vector<PassOp> ops = forward_schedule((int)gs.size(), p, init_plus != 0, d_out != nullptr);
@@ -667,20 +665,37 @@ qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa
     const double bytes = (P.init_plus ? 1.0 : 2.0) * sizeof(C2) * N +
                          ((P.has_phase || P.reduce) ? cost_bytes(ct) * N : 0.0);
     if (G.high)
-      LAUNCH("fwd_high", bytes, s, launch_fwd(P, true, s, nsm));
+      LAUNCH("fwd_high", bytes, s, launch_fwd(P, true, TB, s, nsm));
     else
-      LAUNCH("fwd_low", bytes, s, launch_fwd(P, false, s, nsm));
+      LAUNCH("fwd_low", bytes, s, launch_fwd(P, false, TB, s, nsm));
   }
   return QAOA_OK;
 }
 
+// complex128 at n <= 16: tiles small enough to spread the FP64-bound passes
+// over more SMs, with no more groups than the 4096-amplitude tiles (the
+// partial sums of the tiles fit the workspace: 2^(16-9) * 3 doubles)
 template <typename Real>
-qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
-                           const double *gam, const double *bet, int p, void *state, void *lam,
-                           const Ws &ws, double *d_grad_g, double *d_grad_b, cudaStream_t s) {
+qaoa_status tiled_forward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                          const double *gam, const double *bet, int p, void *state, int init_plus,
+                          const Ws &ws, double *d_out, cudaStream_t s) {
+  if constexpr (sizeof(Real) == 8) {
+    if (n <= 14)
+      return tiled_forward_pl<Real, PlanT9Low, PlanT9High>(n, cost, ct, stats, gam, bet, p, state, init_plus,
+                                                           ws, d_out, s);
+    if (n <= 16)
+      return tiled_forward_pl<Real, PlanT10Low, PlanT10High>(n, cost, ct, stats, gam, bet, p, state,
+                                                             init_plus, ws, d_out, s);
+  }
+  return tiled_forward_pl<Real, typename FwdTB<Real>::Low, typename FwdTB<Real>::High>(
+      n, cost, ct, stats, gam, bet, p, state, init_plus, ws, d_out, s);
+}
+
+template <typename Real, class Low, class High>
+qaoa_status tiled_backward_pl(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                              const double *gam, const double *bet, int p, void *state, void *lam,
+                              const Ws &ws, double *d_grad_g, double *d_grad_b, cudaStream_t s) {
   using C2 = typename C2T<Real>::type;
-  using Low = typename BwdTB<Real>::Low;
-  using High = typename BwdTB<Real>::High;
   const int TB = Low::TB;
   const std::vector<Group> gs = plan_groups(n, TB, kHighC);
   const std::vector<PassOp> ops = adjoint_schedule((int)gs.size(), p);
@@ -742,11 +757,27 @@ qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qao
     const double bytes = (P.init_lambda ? 3.0 : 4.0) * sizeof(C2) * N +
                          ((P.has_phase || P.init_lambda) ? cost_bytes(ct) * N : 0.0);
     if (G.high)
-      LAUNCH("bwd_high", bytes, s, launch_bwd(P, true, s, nsm));
+      LAUNCH("bwd_high", bytes, s, launch_bwd(P, true, TB, s, nsm));
     else
-      LAUNCH("bwd_low", bytes, s, launch_bwd(P, false, s, nsm));
+      LAUNCH("bwd_low", bytes, s, launch_bwd(P, false, TB, s, nsm));
   }
   return QAOA_OK;
+}
+
+template <typename Real>
+qaoa_status tiled_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_cost_stats *stats,
+                           const double *gam, const double *bet, int p, void *state, void *lam,
+                           const Ws &ws, double *d_grad_g, double *d_grad_b, cudaStream_t s) {
+  if constexpr (sizeof(Real) == 8) {
+    if (n <= 14)
+      return tiled_backward_pl<Real, PlanT9Low, PlanT9High>(n, cost, ct, stats, gam, bet, p, state, lam, ws,
+                                                            d_grad_g, d_grad_b, s);
+    if (n <= 16)
+      return tiled_backward_pl<Real, PlanT10Low, PlanT10High>(n, cost, ct, stats, gam, bet, p, state, lam,
+                                                              ws, d_grad_g, d_grad_b, s);
+  }
+  return tiled_backward_pl<Real, typename BwdTB<Real>::Low, typename BwdTB<Real>::High>(
+      n, cost, ct, stats, gam, bet, p, state, lam, ws, d_grad_g, d_grad_b, s);
 }
 
 // ---------------------------------------------------- TMA (complex64) path

@@ -48,10 +48,12 @@ cudaError_t launch_expect(int n, const void *psi, bool c128, const void *cost, i
                           double fmin, double *partials, unsigned *counter, double *out, int which,
                           cudaStream_t s, int nsm);
 
-cudaError_t launch_fwd(const FwdParams<float> &P, bool high, cudaStream_t s, int nsm);
-cudaError_t launch_fwd(const FwdParams<double> &P, bool high, cudaStream_t s, int nsm);
-cudaError_t launch_bwd(const BwdParams<float> &P, bool high, cudaStream_t s, int nsm);
-cudaError_t launch_bwd(const BwdParams<double> &P, bool high, cudaStream_t s, int nsm);
+// tb: log2 of the tile (float: 13 forward, 12 adjoint; double: 9, 10, 12
+// forward, 9, 10, 11 adjoint); other values fail with cudaErrorInvalidValue.
+cudaError_t launch_fwd(const FwdParams<float> &P, bool high, int tb, cudaStream_t s, int nsm);
+cudaError_t launch_fwd(const FwdParams<double> &P, bool high, int tb, cudaStream_t s, int nsm);
+cudaError_t launch_bwd(const BwdParams<float> &P, bool high, int tb, cudaStream_t s, int nsm);
+cudaError_t launch_bwd(const BwdParams<double> &P, bool high, int tb, cudaStream_t s, int nsm);
 
 // Launch profiling (profile.cu): returns a record id, or -1 when disabled.
 int prof_begin(cudaStream_t s);

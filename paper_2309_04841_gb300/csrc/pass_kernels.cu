@@ -579,19 +579,37 @@ static cudaError_t launch_bwd_t(const BwdParams<Real> &P, cudaStream_t s, int ns
   return cudaGetLastError();
 }
 
-cudaError_t launch_fwd(const FwdParams<float> &P, bool high, cudaStream_t s, int nsm) {
+cudaError_t launch_fwd(const FwdParams<float> &P, bool high, int tb, cudaStream_t s, int nsm) {
+  if (tb != PlanF13Low::TB) return cudaErrorInvalidValue;
   return high ? launch_fwd_t<PlanF13High, float>(P, s, nsm) : launch_fwd_t<PlanF13Low, float>(P, s, nsm);
 }
-cudaError_t launch_fwd(const FwdParams<double> &P, bool high, cudaStream_t s, int nsm) {
-  return high ? launch_fwd_t<PlanT12High, double>(P, s, nsm)
-              : launch_fwd_t<PlanT12Low, double>(P, s, nsm);
+cudaError_t launch_fwd(const FwdParams<double> &P, bool high, int tb, cudaStream_t s, int nsm) {
+  switch (tb) {
+    case 9:
+      return high ? launch_fwd_t<PlanT9High, double>(P, s, nsm) : launch_fwd_t<PlanT9Low, double>(P, s, nsm);
+    case 10:
+      return high ? launch_fwd_t<PlanT10High, double>(P, s, nsm) : launch_fwd_t<PlanT10Low, double>(P, s, nsm);
+    case 12:
+      return high ? launch_fwd_t<PlanT12High, double>(P, s, nsm) : launch_fwd_t<PlanT12Low, double>(P, s, nsm);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
-cudaError_t launch_bwd(const BwdParams<float> &P, bool high, cudaStream_t s, int nsm) {
+cudaError_t launch_bwd(const BwdParams<float> &P, bool high, int tb, cudaStream_t s, int nsm) {
+  if (tb != PlanT12Low::TB) return cudaErrorInvalidValue;
   return high ? launch_bwd_t<PlanT12High, float>(P, s, nsm) : launch_bwd_t<PlanT12Low, float>(P, s, nsm);
 }
-cudaError_t launch_bwd(const BwdParams<double> &P, bool high, cudaStream_t s, int nsm) {
-  return high ? launch_bwd_t<PlanT11High, double>(P, s, nsm)
-              : launch_bwd_t<PlanT11Low, double>(P, s, nsm);
+cudaError_t launch_bwd(const BwdParams<double> &P, bool high, int tb, cudaStream_t s, int nsm) {
+  switch (tb) {
+    case 9:
+      return high ? launch_bwd_t<PlanT9High, double>(P, s, nsm) : launch_bwd_t<PlanT9Low, double>(P, s, nsm);
+    case 10:
+      return high ? launch_bwd_t<PlanT10High, double>(P, s, nsm) : launch_bwd_t<PlanT10Low, double>(P, s, nsm);
+    case 11:
+      return high ? launch_bwd_t<PlanT11High, double>(P, s, nsm) : launch_bwd_t<PlanT11Low, double>(P, s, nsm);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace qaoa

@@ -86,7 +86,21 @@ using PlanT11Low = Plan<11, 4, 128, 4, 3, 0x0780, 0x001F, 0x0060,
 using PlanT11High = Plan<11, 4, 128, 4, 2, 0x0780, 0x001F, 0x0060,
                          0x00F0, 0x010F, 0x0600>;
 
+// 1024- and 512-amplitude tiles for complex128 at n <= 16 / n <= 14: the
+// same number of groups as the 4096-amplitude tiles there, but 4-8 times as
+// many CTAs for the FP64-bound rotations.
+using PlanT10Low = Plan<10, 4, 64, 4, 3, 0x03C0, 0x001F, 0x0020,
+                        0x000F, 0x01F0, 0x0200, 0x00F0, 0x010F, 0x0200>;
+using PlanT10High = Plan<10, 4, 64, 4, 2, 0x03C0, 0x001F, 0x0020,
+                         0x00F0, 0x010F, 0x0200>;
+using PlanT9Low = Plan<9, 4, 32, 4, 3, 0x01E0, 0x001F, 0x0000,
+                       0x000F, 0x01F0, 0x0000, 0x00F0, 0x010F, 0x0000>;
+using PlanT9High = Plan<9, 4, 32, 4, 2, 0x01E0, 0x001F, 0x0000,
+                        0x00F0, 0x010F, 0x0000>;
+
 static_assert(PlanF13Low::valid() && PlanF13High::valid(), "bad F13 plan");
+static_assert(PlanT10Low::valid() && PlanT10High::valid(), "bad T10 plan");
+static_assert(PlanT9Low::valid() && PlanT9High::valid(), "bad T9 plan");
 static_assert(PlanT12Low::valid() && PlanT12High::valid(), "bad T12 plan");
 static_assert(PlanT11Low::valid() && PlanT11High::valid(), "bad T11 plan");
 

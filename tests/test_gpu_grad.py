@@ -102,6 +102,24 @@ def test_grad_forced_pairs_vs_oracle(Q, monkeypatch, n, p):
     assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < 1e-4
 
 
+@pytest.mark.parametrize("st,tol", [("c64", 1e-4), ("c128", 1e-9)])
+@pytest.mark.parametrize("n,p", [(13, 3), (16, 4)])
+def test_grad_f64_costs_vs_oracle(Q, n, p, st, tol):
+    # float64 costs take the tiled passes for both state types (reduced-form
+    # rotations, the dropped factors folded into the phase and the last pass,
+    # each round's gradient sums weighted back)
+    terms = I.random_terms(n, 24, 7, max_order=3, integer=False)
+    f = oracle.costs_terms_real(n, terms)
+    fd = Q.precompute_costs(n, terms, Q.COST_F64)
+    stats = Q.cost_stats_compute(fd)
+    g = I.angles(p, 60 + n, 0, 0.4)
+    b = I.angles(p, 61 + n)
+    out = dev_np(Q.grad(fd, stats, g, b, state_type=Q.C64 if st == "c64" else Q.C128))
+    E, dg, db = oracle.grad(n, f, g, b)
+    assert abs(out[0] - E) <= (1e-5 if st == "c64" else 1e-10) * max(1.0, abs(E))
+    assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < tol
+
+
 def test_grad_pair_plans_agree_n26(Q, monkeypatch):
     # the same gradient from the plain adjoint plan and from the plan with
     # every HIGH group on a cluster pair (n = 26: {12-20}, {17-25} rotating
