@@ -150,11 +150,26 @@ __device__ __forceinline__ void st_async(uint32_t addr, float2 v, uint32_t bar) 
                "f"(v.x), "f"(v.y), "r"(bar)
                : "memory");
 }
-// Arrival on the partner's mbarrier without memory ordering: callers issue
-// it after using the values of the shared-memory loads it covers, so those
-// loads have completed.
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar) {
-  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+// Arrival on the partner's mbarrier without memory ordering.  The loads it
+// covers must have returned before it issues: `dep` is a value computed from
+// every register those loads wrote and `zero` a runtime zero, so the address
+// (bar + (dep & zero)) carries a data dependency on all of them that neither
+// the compiler nor the assembler can drop (one warp-wide shared load returns
+// for all lanes at once, so lane 0's registers cover the warp).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar, uint32_t dep, uint32_t zero) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar + (dep & zero))
+               : "memory");
+}
+
+// Bits of every value of the two vectors folded into one word (the
+// dependency of mbar_arrive_remote where no other result depends on them all).
+template <int N>
+__device__ __forceinline__ uint32_t fold_bits(const float2 (&v)[N], const float2 (&w)[N]) {
+  uint32_t d = 0;
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+    d ^= __float_as_uint(v[r].x) ^ __float_as_uint(v[r].y) ^ __float_as_uint(w[r].x) ^ __float_as_uint(w[r].y);
+  return d;
 }
 __device__ __forceinline__ bool mbar_try_cl(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
@@ -1012,8 +1027,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
 // the slots with that bit flipped -- exactly the slots the partner is
 // vacating; the bytes are counted on the partner's exchange mbarrier
 // (complete_tx), on which it waits.  Before pushing, a CTA waits until the
-// partner's 8 warps have signalled (a relaxed remote arrive after using the
-// values they loaded) that they have read those slots.  Sweep 1 rotates
+// partner's 8 warps have signalled (a relaxed remote arrive whose address
+// depends on every value they loaded) that they have read those slots.  Sweep 1 rotates
 // round 0 (tile bits 8..11) in L0, exchanges, then round 1 (tile bits 4..7
 // and, by shuffles, tile bit 12) in L1; sweep 2 (pivots) the reverse, back
 // to L0.  The phase runs in L1, so those passes load the cost tile of the
@@ -1182,9 +1197,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_pair(const __grid_constant_
     }
   };
   // this warp has used what it loaded: the partner may overwrite those slots
-  auto signal = [&](uint32_t rbar) {
+  // (dep: computed from every value this thread loaded for the slots)
+  const uint32_t zero = rank >> 1;  // 0 in a two-CTA cluster, unknown to the compiler
+  auto signal = [&](uint32_t rbar, uint32_t dep) {
     __syncwarp();
-    if (lane == 0) mbar_arrive_remote(rbar);
+    if (lane == 0) mbar_arrive_remote(rbar, dep, zero);
   };
 
   if (tid == 0 && first < nunits) issue(first, need_cost);
@@ -1216,7 +1233,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_pair(const __grid_constant_
     }
     float a1 = 0.f, ag = 0.f, a2 = 0.f;
     unrot_tw<EB, false>(v, w, P.s1.m[0], 0u, P.tau1, P.form1, P.w1[0], a1);
-    signal(remote(&xbar[0]));
+    // a1 now depends on every loaded value when the round rotates anything
+    signal(remote(&xbar[0]), P.s1.m[0] ? __float_as_uint(a1) : fold_bits(v, w));
     // L0 -> L1
     const bool fr1 = mbar_wait_cl(&xbar[0], par);
     flag(fr1);
@@ -1228,7 +1246,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_pair(const __grid_constant_
     lds_round<PL, 1, SW>(v, bv);
     lds_round<PL, 1, SW>(w, bw);
     unrot_tw<EB, true>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
-    if constexpr (H2) signal(remote(&xbar[2]));
+    if constexpr (H2) signal(remote(&xbar[2]), (P.s1.m[1] | P.s1.lm[1]) ? __float_as_uint(a1) : fold_bits(v, w));
     if constexpr (!PH && !H2) release(U);
     if constexpr (PH) {
       unphase_any<PL, 1>(v, w, cb, P, tab, ag, PairCostIdx());
