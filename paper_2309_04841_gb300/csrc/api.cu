@@ -70,21 +70,22 @@ qaoa_status cuda_fail(cudaError_t e, const char *where) {
   } while (0)
 
 // Profile label of a TMA pass: "fwd_high.k7" etc.  Group kind g: 0 LOW, 1
-// HIGH, 2 HIGH on a cluster pair ("bwd_pair").  Kind bits: forward 1 = first
+// HIGH, 2 HIGH on a cluster pair ("bwd_pair"), 3 HIGH on one 512-thread CTA
+// ("bwd_wide").  Kind bits: forward 1 = first
 // sweep, 2 = phase, 4 = second sweep, 8 = energy / overlap; adjoint (the
 // first un-mix sweep is always there) 2 = d/d gamma + un-phase, 4 = second
 // un-mix sweep, 8 = lambda = f psi.
 const char *tma_pass_name(bool fwd, int g, int k) {
-  static char names[2][3][16][24];
+  static char names[2][4][16][24];
   static std::once_flag once;
   std::call_once(once, [] {
-    static const char *gn[3] = {"low", "high", "pair"};
+    static const char *gn[4] = {"low", "high", "pair", "wide"};
     for (int f = 0; f < 2; ++f)
-      for (int h = 0; h < 3; ++h)
+      for (int h = 0; h < 4; ++h)
         for (int j = 0; j < 16; ++j)
           snprintf(names[f][h][j], sizeof(names[f][h][j]), "%s_%s.k%d", f ? "fwd" : "bwd", gn[h], j);
   });
-  return names[fwd ? 1 : 0][g < 0 ? 0 : g > 2 ? 2 : g][k & 15];
+  return names[fwd ? 1 : 0][g < 0 ? 0 : g > 3 ? 3 : g][k & 15];
 }
 
 int num_sms() {
@@ -344,6 +345,16 @@ std::vector<Group> tma_groups(int n, int TB) {
 // overrides the choice: "never" takes the plain plan, "always" makes every
 // HIGH group a cluster pair (for profiling and cross-checks of the pair
 // kernels at any size); unset or anything else is the rule above.
+// The 9-qubit groups run on one 512-thread CTA per 2^13-amplitude tile, except
+// the passes that end with the un-phase (the last pass), which take the
+// cluster pair: with one CTA per SM that pass's next load could only start
+// after its phase.  QAOA_ADJOINT_WIDE=pair puts every pass of those groups on
+// the pair (for tests and comparison).
+bool adjoint_wide_enabled() {
+  const char *e = getenv("QAOA_ADJOINT_WIDE");
+  return !(e && !strcmp(e, "pair"));
+}
+
 int adjoint_pairs_mode() {
   const char *e = getenv("QAOA_ADJOINT_PAIRS");
   if (!e) return 0;
@@ -910,6 +921,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
   const int nsm = num_sms();
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
   static TmaBwdParams P;
+  const bool use_wide = adjoint_wide_enabled();
   static std::mutex *mu = new std::mutex();
   std::lock_guard<std::mutex> lock(*mu);
   std::complex<double> sig = 1.0;  // common scale psi and lambda carry
@@ -917,17 +929,23 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     const Group &G = gs[op.group];
     memset(&P, 0, sizeof(P));
     const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
-    CK(make_tile_map(&P.map_psi, state, n, TB, h, c, 8, 128), "tensor map (psi)");
-    CK(make_tile_map(&P.map_lam, lam, n, TB, h, c, 8, 128), "tensor map (lambda)");
+    // a 9-qubit group's pass: one 512-thread CTA per tile, or the cluster pair
+    const bool wide = G.cl && use_wide && !(op.lp >= 0 && op.l2 < 0);
+    const int TBg = wide ? PlanTmaB13High::TB : TB;
+    CK(make_tile_map(&P.map_psi, state, n, TBg, h, c, 8, 128), "tensor map (psi)");
+    CK(make_tile_map(&P.map_lam, lam, n, TBg, h, c, 8, 128), "tensor map (lambda)");
     P.psi = reinterpret_cast<float2 *>(state);
     P.lam = reinterpret_cast<float2 *>(lam);
-    if (G.cl && op.lp >= 0)
+    if (wide)
+      CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TBg, h, c, (int)cost_bytes(ct), 0),
+         "tensor map (cost)");
+    else if (G.cl && op.lp >= 0)
       CK(make_pair_cost_map(&P.map_cost, const_cast<void *>(cost), n, h, (int)cost_bytes(ct)),
          "tensor map (pair cost)");
     else
       CK(make_tile_map(&P.map_cost, const_cast<void *>(cost), n, TB, h, c, (int)cost_bytes(ct), 0),
          "tensor map (cost)");
-    P.ntiles = 1ull << (n - TB);
+    P.ntiles = 1ull << (n - TBg);
     P.h = h;
     P.c = c;
     P.cost_kind = cost_kind(ct);
@@ -939,8 +957,10 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     pair_sweep.m[0] = (uint8_t)((G.rot >> 8) & 0xFu);
     pair_sweep.m[1] = (uint8_t)((G.rot >> 4) & 0xFu);
     pair_sweep.lm[1] = (uint8_t)(((G.rot >> TB) & 1u) << 4);
-    P.cluster = G.cl;
-    P.s1 = G.cl ? pair_sweep : G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
+    P.cluster = wide ? 2 : G.cl ? 1 : 0;
+    P.s1 = wide   ? make_sweep<PlanTmaB13High>(G.rot, true)
+           : G.cl ? pair_sweep
+           : G.high ? make_sweep<High>(G.rot, true) : make_sweep<Low>(G.rot, true);
     {
       const TanRot R = tan_rot(bet[op.l1], true);
       P.tau1 = R.tau;
@@ -963,7 +983,9 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
       P.out_g = d_grad_g + op.lp;
     }
     if (op.l2 >= 0) {
-      P.s2 = G.cl ? pair_sweep : G.high ? make_sweep<High>(G.rot, false) : make_sweep<Low>(G.rot, false);
+      P.s2 = wide   ? make_sweep<PlanTmaB13High>(G.rot, false)
+             : G.cl ? pair_sweep
+             : G.high ? make_sweep<High>(G.rot, false) : make_sweep<Low>(G.rot, false);
       const TanRot R = tan_rot(bet[op.l2], true);
       P.tau2 = R.tau;
       P.form2 = R.form;
@@ -987,7 +1009,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     const double bytes = (32.0 - (P.init_lambda ? 8.0 : 0.0) - (P.untwist ? 8.0 : 0.0)) * N +
                          ((P.has_phase || P.init_lambda) ? cost_bytes(ct) * N : 0.0);
     const int kind = (P.has_phase ? 2 : 0) | (op.l2 >= 0 ? 4 : 0) | (P.init_lambda ? 8 : 0);
-    LAUNCH_N(tma_pass_name(false, G.cl ? 2 : G.high ? 1 : 0, kind), bytes, s,
+    LAUNCH_N(tma_pass_name(false, wide ? 3 : G.cl ? 2 : G.high ? 1 : 0, kind), bytes, s,
              ct == QAOA_COST_U16 ? launch_bwd_tma_u16(P, G.high, s, nsm) : launch_bwd_tma(P, G.high, s, nsm));
   }
   return QAOA_OK;

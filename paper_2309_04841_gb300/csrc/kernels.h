@@ -71,6 +71,12 @@ using PlanTmaB12High = Plan<12, 4, 256, 0, 2, 0x0F00, 0x001F, 0x00E0,
                             0x00F0, 0x010F, 0x0E00>;
 static_assert(PlanTmaF13Low::valid() && PlanTmaF13High::valid(), "bad TMA F13 plan");
 static_assert(PlanTmaB12Low::valid() && PlanTmaB12High::valid(), "bad TMA B12 plan");
+// Adjoint HIGH groups of 9 qubits on one 512-thread CTA per SM ("wide"): the
+// 2^13-amplitude tile of psi and lambda (16 contiguous amplitudes x rows
+// h..h+8, 128 KB) in one CTA; round 0 holds tile bits 8-11 in registers,
+// round 1 tile bits 4-7 and tile bit 12 as lane bit 4 (a shuffle rotation).
+using PlanTmaB13High = Plan<13, 4, 512, 0, 2, 0x0F00, 0x001F, 0x10E0, 0x00F0, 0x100F, 0x0F00>;
+static_assert(PlanTmaB13High::valid(), "bad TMA B13 plan");
 
 // The TMA passes hold vectors in the twisted basis s(x) = (-i)^popc(x) psi(x),
 // where exp(-i b X_q) acts on a pair as the real rotation
@@ -142,9 +148,10 @@ struct alignas(64) TmaBwdParams {
   float wg;           // |scale|^2 weight of the d/d gamma inner product
   int has_phase, init_lambda;
   int untwist;  // last pass: psi back to the standard basis, lambda not stored
-  // Cluster pair (HIGH group of 9 new qubits, c = 4): two CTAs hold the two
-  // halves of a 2^13-amplitude tile (k_bwd_pair); map_cost is then the
-  // pair cost map of the phase layout for passes with a phase.
+  // HIGH group of 9 new qubits (c = 4) on a 2^13-amplitude tile: 1 = cluster
+  // pair, two CTAs holding its two halves (k_bwd_pair; map_cost is then the
+  // pair cost map of the phase layout for passes with a phase); 2 = one
+  // 512-thread CTA (k_bwd_tma with PlanTmaB13High); 0 = neither
   int cluster;
   double *partials;
   unsigned *counter;

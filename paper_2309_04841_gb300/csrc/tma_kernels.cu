@@ -108,8 +108,9 @@ __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, TC c
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-// Barrier among the CTA's 256 threads (named barrier 1).
-__device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// Barrier among the CTA's NT threads (named barrier 1).
+template <int NT = 256>
+__device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
 
 // ---- cluster pairs (two CTAs, distributed shared memory)
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -369,7 +370,7 @@ __device__ __forceinline__ void sts_round(const float2 (&v)[PL::NREG], float2 *b
 template <class PL, int RF, int RT, int SW>
 __device__ __forceinline__ void xp(float2 (&v)[PL::NREG], float2 *buf) {
   sts_round<PL, RF, SW>(v, buf);
-  cbar();
+  cbar<PL::NT>();
   lds_round<PL, RT, SW>(v, buf);
 }
 
@@ -378,7 +379,7 @@ __device__ __forceinline__ void xp(float2 (&v)[PL::NREG], float2 *buf) {
 template <class PL, int RF, int RT, int SW, class F>
 __device__ __forceinline__ void xp_hook(float2 (&v)[PL::NREG], float2 *buf, F at_barrier) {
   sts_round<PL, RF, SW>(v, buf);
-  cbar();
+  cbar<PL::NT>();
   at_barrier();
   lds_round<PL, RT, SW>(v, buf);
 }
@@ -389,7 +390,7 @@ __device__ __forceinline__ void xp_pair(float2 (&v)[PL::NREG], float2 (&w)[PL::N
                                         float2 *bw, F at_barrier) {
   sts_round<PL, RF, SW>(v, bv);
   sts_round<PL, RF, SW>(w, bw);
-  cbar();
+  cbar<PL::NT>();
   at_barrier();
   lds_round<PL, RT, SW>(v, bv);
   lds_round<PL, RT, SW>(w, bw);
@@ -512,24 +513,24 @@ __device__ __forceinline__ void eo_round(const float2 (&v)[PL::NREG], const Cost
   }
 }
 
-// Sum of K doubles over the 256 compute threads (fixed order); thread 0 gets it.
-template <int K>
+// Sum of K doubles over the CTA's NT threads (fixed order); thread 0 gets it.
+template <int K, int NT = 256>
 __device__ __forceinline__ void csum(double (&a)[K], double *red) {
 #pragma unroll
   for (int k = 0; k < K; ++k)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
   const int w = threadIdx.x >> 5;
-  cbar();
+  cbar<NT>();
   if ((threadIdx.x & 31) == 0)
 #pragma unroll
     for (int k = 0; k < K; ++k) red[w * K + k] = a[k];
-  cbar();
+  cbar<NT>();
   if (threadIdx.x == 0)
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double s = 0.0;
-      for (int i = 0; i < 8; ++i) s += red[i * K + k];
+      for (int i = 0; i < NT / 32; ++i) s += red[i * K + k];
       a[k] = s;
     }
 }
@@ -615,7 +616,7 @@ __device__ __forceinline__ unsigned char *aligned_base(unsigned char *raw) {
 
 static size_t smem_bytes(int tb, bool two, bool cost) {
   const size_t te = (size_t)1 << tb;
-  return 1024 + te * 8 * (two ? 2 : 1) + (cost ? te * kCW : 0) + kPhaseTabEntries * 8 + 32 + 8 * 3 * 8;
+  return 1024 + te * 8 * (two ? 2 : 1) + (cost ? te * kCW : 0) + kPhaseTabEntries * 8 + 32 + 16 * 3 * 8;
 }
 
 // ------------------------------------------------------------- forward
@@ -858,8 +859,9 @@ __device__ __forceinline__ void unphase_any(float2 (&v)[PL::NREG], float2 (&w)[P
 
 // The state tiles use the TMA 128-byte swizzle (16- to 64-amplitude segments).
 template <class PL, int K>
-__global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
+__global__ void __launch_bounds__(PL::NT, 512 / PL::NT) k_bwd_tma(const __grid_constant__ TmaBwdParams P) {
   constexpr int NREG = PL::NREG, NR = PL::NR, EB = PL::EB, SW = 128;
+  constexpr bool LN = PL::NT == 512;  // the 512-thread plan rotates tile bit 12 across lanes
   constexpr bool PH = (K & kPH) != 0, H2 = (K & kH2) != 0, INIT = (K & kINIT) != 0;
   constexpr bool need_cost = PH || INIT;
   constexpr int RS = H2 ? 0 : NR - 1;  // the round the tiles are stored from
@@ -876,7 +878,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
   const int midbits = P.h - P.c;
   __shared__ int s_abort;
 
-  if (PH && P.ph.mode == 0) fill_phase_tab<kThreads>(tab, P.ph);
+  if (PH && P.ph.mode == 0) fill_phase_tab<PL::NT>(tab, P.ph);
   if (tid == 0) {
     s_abort = 0;
     mbar_init(full, 1);
@@ -916,7 +918,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
   };
   // after the tile's last shared-memory read: the buffers go to the next load
   auto release = [&](uint64_t T) {
-    cbar();
+    cbar<PL::NT>();
     if (tid == 0 && T + gridDim.x < P.ntiles && !abort_now) issue(T + gridDim.x, need_cost && !early_cost);
   };
 
@@ -949,17 +951,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
       lds_round<PL, 0, SW>(w, bw);
     }
     float a1 = 0.f, ag = 0.f, a2 = 0.f;
-    unrot_tw<EB, false>(v, w, P.s1.m[0], P.s1.lm[0], P.tau1, P.form1, P.w1[0], a1);
+    unrot_tw<EB, LN>(v, w, P.s1.m[0], P.s1.lm[0], P.tau1, P.form1, P.w1[0], a1);
     if constexpr (INIT && early_cost)
       xp_pair<PL, 0, 1, SW>(v, w, bv, bw, [&] { read_abort(); cost_next(T); });
     else
       xp_pair<PL, 0, 1, SW>(v, w, bv, bw, [&] { read_abort(); });
     if constexpr (NR == 2 && !PH && !H2) release(T);
-    unrot_tw<EB, false>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
+    unrot_tw<EB, LN>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
     if constexpr (NR == 3) {
       xp_pair<PL, 1, 2, SW>(v, w, bv, bw, NoHook());
       if constexpr (!PH && !H2) release(T);
-      unrot_tw<EB, false>(v, w, P.s1.m[2], P.s1.lm[2], P.tau1, P.form1, P.w1[2], a1);
+      unrot_tw<EB, LN>(v, w, P.s1.m[2], P.s1.lm[2], P.tau1, P.form1, P.w1[2], a1);
     }
     if constexpr (PH) {
       // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
@@ -967,13 +969,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
       if constexpr (!H2) release(T);
     }
     if constexpr (H2) {
-      unrot_tw<EB, false>(v, w, P.s2.m[NR - 1], P.s2.lm[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
+      unrot_tw<EB, LN>(v, w, P.s2.m[NR - 1], P.s2.lm[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
       if constexpr (NR == 3) {
         if constexpr (PH && early_cost)
           xp_pair<PL, 2, 1, SW>(v, w, bv, bw, [&] { cost_next(T); });
         else
           xp_pair<PL, 2, 1, SW>(v, w, bv, bw, NoHook());
-        unrot_tw<EB, false>(v, w, P.s2.m[1], P.s2.lm[1], P.tau2, P.form2, P.w2[1], a2);
+        unrot_tw<EB, LN>(v, w, P.s2.m[1], P.s2.lm[1], P.tau2, P.form2, P.w2[1], a2);
         xp_pair<PL, 1, 0, SW>(v, w, bv, bw, NoHook());
       } else if constexpr (PH && early_cost) {
         xp_pair<PL, 1, 0, SW>(v, w, bv, bw, [&] { cost_next(T); });
@@ -981,7 +983,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
         xp_pair<PL, 1, 0, SW>(v, w, bv, bw, NoHook());
       }
       release(T);
-      unrot_tw<EB, false>(v, w, P.s2.m[0], P.s2.lm[0], P.tau2, P.form2, P.w2[0], a2);
+      unrot_tw<EB, LN>(v, w, P.s2.m[0], P.s2.lm[0], P.tau2, P.form2, P.w2[0], a2);
     }
     if (P.untwist) {
       // psi back to the standard basis (lambda is scratch from here on)
@@ -997,7 +999,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_bwd_tma(const __grid_constant__
   }
   drain(abort_now, full, i);
   double a[3] = {acc1.value(), accg.value(), acc2.value()};
-  csum<3>(a, red);
+  csum<3, PL::NT>(a, red);
   if (tid == 0) {
     P.partials[blockIdx.x * 3] = a[0];
     P.partials[blockIdx.x * 3 + 1] = a[1];
@@ -1612,12 +1614,12 @@ static cudaError_t launch_bwd_tma_t(const TmaBwdParams &P, cudaStream_t s, int n
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e != cudaSuccess) return e;
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, mx) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, PL::NT, mx) != cudaSuccess || b < 1) b = 1;
     nb = b;
   }
   uint64_t grid = (uint64_t)nsm * nb;
   if (grid > P.ntiles) grid = P.ntiles;
-  kern<<<(unsigned)grid, kThreads, smem, s>>>(P);
+  kern<<<(unsigned)grid, PL::NT, smem, s>>>(P);
   return cudaGetLastError();
 }
 
@@ -1748,6 +1750,10 @@ cudaError_t QAOA_TMA_FN(launch_bwd_tma)(const TmaBwdParams &P, bool high, cudaSt
     if ((!P.cluster && (P.s1.lm[r] | P.s2.lm[r]) != 0) || __builtin_popcount(P.s1.lm[r]) > 1 ||
         __builtin_popcount(P.s2.lm[r]) > 1)
       return cudaErrorInvalidValue;
+  if (P.cluster == 2) {  // a HIGH group of up to 9 qubits on one 512-thread CTA
+    if (!high || P.c != 4 || P.h < 4) return cudaErrorInvalidValue;
+    return dispatch_bwd<PlanTmaB13High>(P, s, nsm);
+  }
   if (P.cluster) {
     // a HIGH group of up to 9 qubits on a pair: 16-amplitude segments,
     // rotations within the two layouts' sets (round 0: 4 register bits;

@@ -77,13 +77,17 @@ def test_grad_cluster_pair_vs_oracle(Q, cost, n, p):
     assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < 1e-4
 
 
+@pytest.mark.parametrize("impl", ["wide", "pair"])
 @pytest.mark.parametrize("n,p", [(13, 2), (17, 3), (22, 2), (24, 2)])
-def test_grad_forced_pairs_vs_oracle(Q, monkeypatch, n, p):
-    # every HIGH group of the adjoint on a cluster pair, including groups that
-    # rotate only some of the pair's 9 qubits: n = 13 only the split qubit,
-    # n = 17 the round-0 bits and the split qubit, n = 22 a full pair then the
-    # split qubit alone, n = 24 a full pair then three qubits
+def test_grad_forced_pairs_vs_oracle(Q, monkeypatch, n, p, impl):
+    # every HIGH group of the adjoint a 9-qubit group (one 512-thread CTA per
+    # 2^13-amplitude tile, or a cluster pair for every pass), including groups
+    # that rotate only some of the 9 qubits: n = 13 only the top one, n = 17
+    # round 0's bits and the top one, n = 22 a full group then the top qubit
+    # alone, n = 24 a full group then three qubits
     monkeypatch.setenv("QAOA_ADJOINT_PAIRS", "always")
+    if impl == "pair":
+        monkeypatch.setenv("QAOA_ADJOINT_WIDE", "pair")
     f = oracle.labs_costs(n).astype(float)
     fd = Q.labs_costs(n)
     stats = Q.cost_stats_compute(fd)
@@ -96,7 +100,11 @@ def test_grad_forced_pairs_vs_oracle(Q, monkeypatch, n, p):
         kinds = Q.profile_read()
     finally:
         Q.profile_enable(False)
-    assert any(k.startswith("bwd_pair") for k in kinds) and not any(k.startswith("bwd_high") for k in kinds)
+    assert not any(k.startswith("bwd_high") for k in kinds)
+    if impl == "pair":
+        assert any(k.startswith("bwd_pair") for k in kinds) and not any(k.startswith("bwd_wide") for k in kinds)
+    else:
+        assert any(k.startswith("bwd_wide") for k in kinds)
     E, dg, db = oracle.grad(n, f, g, b)
     assert abs(out[0] - E) <= 1e-5 * max(1.0, abs(E))
     assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < 1e-4
@@ -118,6 +126,24 @@ def test_grad_f64_costs_vs_oracle(Q, n, p, st, tol):
     E, dg, db = oracle.grad(n, f, g, b)
     assert abs(out[0] - E) <= (1e-5 if st == "c64" else 1e-10) * max(1.0, abs(E))
     assert rel(np.concatenate([out[2:2 + p], out[2 + p:]]), np.concatenate([dg, db])) < tol
+
+
+def test_grad_wide_and_pair_agree_n30_p2(Q, monkeypatch):
+    # the headline plan's 9-qubit groups on the 512-thread CTA and on cluster
+    # pairs: the same arithmetic in another order, agreement to rounding
+    w = I.workload("labs30_p2")
+    n = w["n"]
+    fd = Q.labs_costs(n)
+    stats = Q.cost_stats_compute(fd)
+    g, b = I.workload_angles(w)
+    res = {}
+    for impl in ("wide", "pair"):
+        if impl == "pair":
+            monkeypatch.setenv("QAOA_ADJOINT_WIDE", "pair")
+        res[impl] = dev_np(Q.grad(fd, stats, g, b))
+    a, c = res["wide"], res["pair"]
+    assert abs(a[0] - c[0]) <= 1e-7 * abs(c[0])
+    assert rel(a[2:], c[2:]) < 1e-5
 
 
 def test_grad_pair_plans_agree_n26(Q, monkeypatch):
