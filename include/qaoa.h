@@ -372,11 +372,13 @@ qaoa_status qaoa_overlap(int n, const void *d_state, qaoa_state_type st,
  *     E and O of the forward final state.
  * Asynchronous.
  * Plan (complex64, n >= 13): the backward passes rotate the qubits in
- * groups; a group of up to 9 qubits can run on a pair of CTAs that exchange
- * halves of a 2^13-amplitude tile, taken where it saves a group (n = 21, 29,
- * 30).  The environment variable QAOA_ADJOINT_PAIRS, read at each call,
- * overrides that choice: "never" or "always" (every group above the lowest
- * 12 qubits on a pair).  Results agree across plans to rounding.
+ * groups; a group of up to 9 qubits on a 2^13-amplitude tile is taken where
+ * it saves a group (n = 21, 29, 30).  Its passes run on one 512-thread CTA
+ * per tile, the last pass on a pair of CTAs that exchange halves of the tile.
+ * Environment variables, read at each call: QAOA_ADJOINT_PAIRS = "never" (no
+ * such groups) or "always" (every group above the lowest 12 qubits is one);
+ * QAOA_ADJOINT_WIDE = "pair" (every pass of those groups on CTA pairs).
+ * Results agree across plans to rounding.
  */
 qaoa_status qaoa_grad(int n, const void *d_costs, qaoa_cost_type ct,
                       const qaoa_cost_stats *stats, const double *gammas,
