@@ -332,10 +332,12 @@ std::vector<Group> tma_groups(int n, int TB) {
   return best;
 }
 
-// Adjoint groups with cluster pairs: the LOW group (qubits 0..TB-1), then
+// Adjoint groups with 9-qubit groups: the LOW group (qubits 0..TB-1), then
 // HIGH groups of 2^c contiguous amplitudes (c = 4) times TB - c local rows,
-// of which a cluster group adds one more row qubit (h + TB - c) held by the
-// other CTA of a pair: TB - c + 1 new qubits per group instead of TB - c.
+// of which a 9-qubit group (`cl`) adds one more row qubit (h + TB - c): its
+// 2^13-amplitude tile runs on one 512-thread CTA, or split over the two CTAs
+// of a cluster pair (see tma_backward): TB - c + 1 new qubits per group
+// instead of TB - c.
 // Taken where it needs fewer groups than the plain plan (LABS n = 30:
 // {0-11}, {12-20}, {21-29} -- three groups, two passes per layer, instead of
 // four; also n = 21, 29); only as many groups as necessary are cluster pairs.
@@ -343,7 +345,7 @@ std::vector<Group> tma_groups(int n, int TB) {
 // groups; measured at n = 29: 114.1 ms per LABS p = 10 evaluation against
 // 108.8 ms with the pair.)  The environment variable QAOA_ADJOINT_PAIRS
 // overrides the choice: "never" takes the plain plan, "always" makes every
-// HIGH group a cluster pair (for profiling and cross-checks of the pair
+// HIGH group a 9-qubit group (for profiling and cross-checks of those
 // kernels at any size); unset or anything else is the rule above.
 // The 9-qubit groups run on one 512-thread CTA per 2^13-amplitude tile, except
 // the passes that end with the un-phase (the last pass), which take the

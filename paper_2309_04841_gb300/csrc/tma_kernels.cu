@@ -3,7 +3,8 @@
 // Algorithm 1 rotations on a tile window (in the twisted basis, packed fp32x2
 // FMA), the phase of Algorithm 3 (conflict-free digit tables), the fused
 // energy/overlap, and the adjoint inner products:
-//   * persistent CTAs, two per SM, 256 threads each, one tile buffer each;
+//   * persistent CTAs, two per SM, 256 threads each, one tile buffer each
+//     (the adjoint's 9-qubit groups: one 512-thread CTA per SM);
 //   * thread 0 issues cp.async.bulk.tensor loads (mbarrier complete_tx) of the
 //     state tile (and the cost tile) with the TMA 128-byte swizzle; the
 //     compute rounds are laid out so that every shared-memory access of the
