@@ -377,7 +377,8 @@ qaoa_status qaoa_overlap(int n, const void *d_state, qaoa_state_type st,
  * per tile, the last pass on a pair of CTAs that exchange halves of the tile.
  * Environment variables, read at each call: QAOA_ADJOINT_PAIRS = "never" (no
  * such groups) or "always" (every group above the lowest 12 qubits is one);
- * QAOA_ADJOINT_WIDE = "pair" (every pass of those groups on CTA pairs).
+ * QAOA_ADJOINT_WIDE = "pair" (every pass of those groups on CTA pairs) or
+ * "all" (every pass, the last one too, on the 512-thread CTA).
  * Results agree across plans to rounding.
  */
 qaoa_status qaoa_grad(int n, const void *d_costs, qaoa_cost_type ct,

@@ -349,12 +349,14 @@ std::vector<Group> tma_groups(int n, int TB) {
 // kernels at any size); unset or anything else is the rule above.
 // The 9-qubit groups run on one 512-thread CTA per 2^13-amplitude tile, except
 // the passes that end with the un-phase (the last pass), which take the
-// cluster pair: with one CTA per SM that pass's next load could only start
-// after its phase.  QAOA_ADJOINT_WIDE=pair puts every pass of those groups on
-// the pair (for tests and comparison).
-bool adjoint_wide_enabled() {
+// cluster pair.  QAOA_ADJOINT_WIDE=pair puts every pass of those groups on
+// the pair, =all every pass on the 512-thread CTA (tests and comparison).
+// Returns 0 (pairs), 1 (default), 2 (all).
+int adjoint_wide_mode() {
   const char *e = getenv("QAOA_ADJOINT_WIDE");
-  return !(e && !strcmp(e, "pair"));
+  if (e && !strcmp(e, "pair")) return 0;
+  if (e && !strcmp(e, "all")) return 2;
+  return 1;
 }
 
 int adjoint_pairs_mode() {
@@ -923,7 +925,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
   const int nsm = num_sms();
   CK(cudaMemsetAsync(ws.counter, 0, sizeof(unsigned), s), "memset counter");
   static TmaBwdParams P;
-  const bool use_wide = adjoint_wide_enabled();
+  const int wide_mode = adjoint_wide_mode();
   static std::mutex *mu = new std::mutex();
   std::lock_guard<std::mutex> lock(*mu);
   std::complex<double> sig = 1.0;  // common scale psi and lambda carry
@@ -932,7 +934,7 @@ qaoa_status tma_backward(int n, const void *cost, qaoa_cost_type ct, const qaoa_
     memset(&P, 0, sizeof(P));
     const int h = G.high ? G.h : 4, c = G.high ? G.c : 4;
     // a 9-qubit group's pass: one 512-thread CTA per tile, or the cluster pair
-    const bool wide = G.cl && use_wide && !(op.lp >= 0 && op.l2 < 0);
+    const bool wide = G.cl && (wide_mode == 2 || (wide_mode == 1 && !(op.lp >= 0 && op.l2 < 0)));
     const int TBg = wide ? PlanTmaB13High::TB : TB;
     CK(make_tile_map(&P.map_psi, state, n, TBg, h, c, 8, 128), "tensor map (psi)");
     CK(make_tile_map(&P.map_lam, lam, n, TBg, h, c, 8, 128), "tensor map (lambda)");

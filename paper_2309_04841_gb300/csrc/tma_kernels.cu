@@ -922,6 +922,27 @@ __global__ void __launch_bounds__(PL::NT, 512 / PL::NT) k_bwd_tma(const __grid_c
     cbar<PL::NT>();
     if (tid == 0 && T + gridDim.x < P.ntiles && !abort_now) issue(T + gridDim.x, need_cost && !early_cost);
   };
+  // Passes that end with the un-phase: the vectors go to the next load once
+  // the last round's data is in registers, the costs once the phase has read
+  // them; the mbarrier's one arrive comes with the cost load, so the phase
+  // cannot complete before both loads are counted.
+  constexpr bool late_cost = PH && !H2 && !INIT;
+  auto release_vectors = [&](uint64_t T) {
+    cbar<PL::NT>();
+    if (tid == 0 && T + gridDim.x < P.ntiles && !abort_now) {
+      const TC c = coords(T + gridDim.x);
+      mbar_add_tx(full, 2u * L.tile_bytes);
+      tma_load(bv, &P.map_psi, c, full);
+      tma_load(bw, &P.map_lam, c, full);
+    }
+  };
+  auto release_cost = [&](uint64_t T) {
+    cbar<PL::NT>();
+    if (tid == 0 && T + gridDim.x < P.ntiles && !abort_now) {
+      mbar_expect_tx(full, L.cost_bytes);
+      tma_load(base + L.cost_off, &P.map_cost, coords(T + gridDim.x), full);
+    }
+  };
 
   if (tid == 0 && blockIdx.x < P.ntiles) issue(blockIdx.x, need_cost);
 
@@ -958,16 +979,21 @@ __global__ void __launch_bounds__(PL::NT, 512 / PL::NT) k_bwd_tma(const __grid_c
     else
       xp_pair<PL, 0, 1, SW>(v, w, bv, bw, [&] { read_abort(); });
     if constexpr (NR == 2 && !PH && !H2) release(T);
+    if constexpr (NR == 2 && late_cost) release_vectors(T);
     unrot_tw<EB, LN>(v, w, P.s1.m[1], P.s1.lm[1], P.tau1, P.form1, P.w1[1], a1);
     if constexpr (NR == 3) {
       xp_pair<PL, 1, 2, SW>(v, w, bv, bw, NoHook());
       if constexpr (!PH && !H2) release(T);
+      if constexpr (late_cost) release_vectors(T);
       unrot_tw<EB, LN>(v, w, P.s1.m[2], P.s1.lm[2], P.tau1, P.form1, P.w1[2], a1);
     }
     if constexpr (PH) {
       // d/d gamma: Im <lambda| f |psi>, then un-phase both vectors
       unphase_any<PL, NR - 1>(v, w, cb, P, tab, ag);
-      if constexpr (!H2) release(T);
+      if constexpr (late_cost)
+        release_cost(T);
+      else if constexpr (!H2)
+        release(T);
     }
     if constexpr (H2) {
       unrot_tw<EB, LN>(v, w, P.s2.m[NR - 1], P.s2.lm[NR - 1], P.tau2, P.form2, P.w2[NR - 1], a2);
